@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the synchronous island GA on the paper-scale workload.
+
+Workload (one "step"): the 512x1024 torus of 32-agent islands (16,777,216 agents, 16-byte
+records: trait, counter, 64 one-bit steady-curated hstrat sites), tournament size 5,
+p_del = 0.01, one migrant from each neighbour every generation, 10,000 generations, for the
+adaptive (p_ben = 0.01) and the purifying-only (p_ben = 0) treatment (Sec. 3 of the paper),
+each started from its founder population and followed by pairwise MRCA bounds over 4,096
+uniformly sampled end-state agents (8,386,560 pairs).
+
+Prints one JSON line.  value = agent-generations per second over the timed steps (inputs
+resident in HBM, CUDA events on the run's stream); e2e = the same job through the public API
+with host buffers (create, step, MRCA into pinned host arrays, snapshot into pinned host
+memory, destroy) timed on the host.  --impl reference times the CPU oracle on a bounded
+sample of the same workload on the host cores.  Under torchrun each rank runs an
+independent replica on its own GPU (the path is not sharded).
+"""
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "agent-gens/sec @16.8M agents on 1 GB300; % roofline; batched vs serial"
+UNIT = "agent-gens/s"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--rows", type=int, default=512)
+    p.add_argument("--cols", type=int, default=1024)
+    p.add_argument("--gens", type=int, default=10000)
+    p.add_argument("--sample", type=int, default=4096)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shapes(args, rank):
+    from paper_2405_03605_gb300.workloads import PAPER_ADAPTIVE, PAPER_PURIFYING
+    out = []
+    for i, s in enumerate((PAPER_ADAPTIVE, PAPER_PURIFYING)):
+        out.append(s.with_(rows=args.rows, cols=args.cols, generations=args.gens,
+                           run_id=2 * rank + i))
+    return out
+
+
+def workload_config(args, sh):
+    return {
+        "workload": (f"island GA {args.rows}x{args.cols} torus x {sh.island_size} agents "
+                     f"({sh.n_agents} agents), 16 B records (steady 64x1-bit hstrat), "
+                     f"tournament {sh.tournament_size}, p_del 0.01, 1 migrant/neighbour/gen, "
+                     f"{args.gens} gens, adaptive (p_ben 0.01) + purifying (p_ben 0) runs, "
+                     f"then MRCA bounds over {args.sample} sampled agents"),
+        "rows": args.rows, "cols": args.cols, "island_size": sh.island_size,
+        "agents_per_run": sh.n_agents, "runs_per_step": 2, "generations": args.gens,
+        "record_bytes": 16, "mrca_sample": args.sample,
+        "l2": "no flush: every generation streams the 256 MiB population in and a second "
+              "256 MiB buffer out, both larger than the 129 MB L2",
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        if shutil.which("nvidia-smi") is None:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.f = open(self.path, "w")
+        self.proc = subprocess.Popen(
+            ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+             "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=self.f, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(args, sh, seconds):
+    """The oracle, as it stands, on the same grid: generations until `seconds` elapse."""
+    from oracle import OracleRun
+    threads = os.cpu_count() or 1
+    o = OracleRun(sh.rows, sh.cols, island_size=sh.island_size,
+                  tournament_size=sh.tournament_size, p_ben=sh.p_ben, p_del=sh.p_del,
+                  surface_sites=sh.surface_sites, differentia_bits=sh.differentia_bits,
+                  curation=sh.curation, migrate_every=sh.migrate_every, seed=sh.seed,
+                  run_id=sh.run_id, threads=threads)
+    gens = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(1)
+        gens += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    o.close()
+    return {"value": sh.n_agents * gens / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"adaptive run, full {sh.rows}x{sh.cols}x{sh.island_size} grid, first "
+                      f"{gens} generations ({dt:.1f} s), OpenMP over islands"}
+
+
+def run_reference(args, rank, world):
+    """CPU oracle arm: each step = a bounded sample of the workload on the host cores."""
+    if rank != 0:
+        return
+    sh = shapes(args, 0)[0]
+    from oracle import OracleRun
+    threads = os.cpu_count() or 1
+    o = OracleRun(sh.rows, sh.cols, island_size=sh.island_size,
+                  tournament_size=sh.tournament_size, p_ben=sh.p_ben, p_del=sh.p_del,
+                  surface_sites=sh.surface_sites, differentia_bits=sh.differentia_bits,
+                  curation=sh.curation, migrate_every=sh.migrate_every, seed=sh.seed,
+                  run_id=sh.run_id, threads=threads)
+    gens_per_step = 2
+    for _ in range(args.warmup):
+        o.step(gens_per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(gens_per_step)
+    dt = time.perf_counter() - t0
+    value = sh.n_agents * gens_per_step * args.steps / dt
+    sample = (f"adaptive run, full {sh.rows}x{sh.cols}x{sh.island_size} grid, "
+              f"{gens_per_step} generations per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1000 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(args, sh),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2405_03605_gb300 import build as lib_build
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import sample_agent_ids
+
+    lib_build.build()
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    shs = shapes(args, rank)
+    stream = torch.cuda.Stream()
+    runs = [ga.Run(s, stream=stream) for s in shs]
+    n = args.sample
+    pairs = n * (n - 1) // 2
+    ids_h = sample_agent_ids(shs[0].n_agents, n, seed=42)
+    with torch.cuda.stream(stream):
+        ids_d = torch.from_numpy(ids_h.view(np.int32)).cuda()
+        outs = [(torch.empty(pairs, dtype=torch.int32, device="cuda"),
+                 torch.empty(pairs, dtype=torch.int32, device="cuda")) for _ in runs]
+
+    step_pairs, mrca_pairs = [], []
+
+    def one_step(record):
+        for r, (lo, hi) in zip(runs, outs):
+            r.reset()
+            if record:
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+            r.step(args.gens)
+            if record:
+                e1.record(stream)
+            r.mrca_bounds_device(ids_d, lo, hi)
+            if record:
+                e2.record(stream)
+                step_pairs.append((e0, e1))
+                mrca_pairs.append((e1, e2))
+
+    for _ in range(args.warmup):
+        one_step(False)
+    stream.synchronize()
+    for r in runs:
+        r.sync()
+
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local) if rank == 0 else None
+    launches0 = sum(r.launches for r in runs)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        one_step(True)
+    t_end.record(stream)
+    stream.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    for r in runs:
+        r.sync()
+    launches = sum(r.launches for r in runs) - launches0
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    agent_gens = args.steps * sum(s.n_agents * args.gens for s in shs) * world
+    value = agent_gens / (elapsed_ms / 1000.0)
+
+    # roofline of the island-step kernel: one launch = one generation of one run (migration
+    # every generation), algorithmic bytes per agent = record in + record out + 4 immigrant
+    # records per island = 2G + 4G/N
+    step_ms = sum(a.elapsed_time(b) for a, b in step_pairs)
+    step_launches = args.gens * len(step_pairs)
+    G, N = 16, shs[0].island_size
+    bytes_per_launch = shs[0].n_agents * (2 * G + 4 * G / N)
+    avg_launch_s = step_ms / 1000.0 / step_launches
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    mrca_ms = statistics.mean(a.elapsed_time(b) for a, b in mrca_pairs)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, shs, ids_h, world)
+
+    for r in runs:
+        r.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(args, shs[0], args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {**workload_config(args, shs[0]),
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "island_step_kernel<32,2>",
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "bytes_per_launch": bytes_per_launch,
+                     "avg_launch_us": avg_launch_s * 1e6},
+        "mrca_ms_per_run": mrca_ms,
+        "gpu_launches": launches,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def measure_e2e(args, shs, ids_h, world):
+    """Same job through the public API with host buffers: create (library-allocated
+    workspace), step, MRCA from pinned host ids into pinned host (lo, hi), snapshot into
+    pinned host memory, destroy -- timed on the host around each step."""
+    import numpy as np
+    import torch
+    from paper_2405_03605_gb300 import ga
+
+    n = ids_h.size
+    pairs = n * (n - 1) // 2
+    pin = lambda nbytes: torch.empty(nbytes, dtype=torch.uint8, pin_memory=True).numpy()
+    ids_pin = pin(ids_h.nbytes).view(np.uint32)
+    ids_pin[:] = ids_h
+    lo_pin = pin(pairs * 4).view(np.uint32)
+    hi_pin = pin(pairs * 4).view(np.uint32)
+    rb = 16
+    snaps = [pin(s.n_agents * rb).reshape(s.n_agents, rb) for s in shs]
+    stream = torch.cuda.Stream()
+
+    def job():
+        for s, snap in zip(shs, snaps):
+            r = ga.Run(s, stream=stream, workspace="library")
+            r.step(args.gens)
+            r.mrca_bounds(ids_pin, lo_pin, hi_pin)
+            r.snapshot(snap)
+            r.close()
+
+    job()  # warm-up
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        job()
+        times.append(time.perf_counter() - t0)
+    agent_gens = sum(s.n_agents * args.gens for s in shs) * world
+    dt = statistics.mean(times)
+    return {"value": agent_gens / dt, "unit": UNIT,
+            "h2d_bytes_per_step": int(len(shs) * ids_h.nbytes),
+            "d2h_bytes_per_step": int(sum(s.n_agents * rb for s in shs) + len(shs) * 2 * pairs * 4),
+            "steps": args.e2e_steps, "ms_per_step": dt * 1000}
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

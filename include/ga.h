@@ -1,0 +1,190 @@
+/*
+ * ga.h -- C ABI of libga, the GB300 (sm_103a) trackable island-model genetic algorithm.
+ *
+ * The library runs the per-generation island step of Moreno et al., "Trackable Island-model
+ * Genetic Algorithms at Wafer Scale" (GECCO'24 Companion), Sec. 2, on one GPU: a torus of
+ * islands, each a population of N agents; every generation handles migration first (one
+ * migrant from each of the four cardinal neighbours, replacing randomly chosen members),
+ * then evaluation (fitness = trait), tournament selection (n random picks, ties broken
+ * randomly), mutation of the trait (+1 with p_ben, -1 with p_del; the paper's adaptive vs
+ * purifying-only treatments of Sec. 3 are p_ben > 0 vs p_ben = 0) and the hereditary
+ * stratigraphy (hstrat) update for the elapsed generation; the run halts after the
+ * requested number of generations.  Post hoc, ga_mrca_bounds estimates pairwise relatedness
+ * from the hstrat surfaces (Fig. 1 caption).
+ *
+ * Conventions
+ *   - Every call returns GA_OK (0) or a negative GA_E* code; nothing throws or exits.
+ *   - Host buffers passed in are owned by the caller and only read/written during the call.
+ *   - Device memory: the run's state lives in one device workspace, either supplied by the
+ *     caller (ga_create with a non-NULL workspace; the caller frees it after ga_destroy) or
+ *     allocated by the library (workspace NULL; freed by ga_destroy).
+ *   - All GPU work of a run is enqueued on the stream given in its config (NULL = the
+ *     legacy default stream).  Calls that end in "_device" or ga_step are asynchronous with
+ *     respect to the host; the others synchronise that stream before returning.
+ *   - A ga_run handle is not thread-safe; distinct handles may be used from distinct threads.
+ *   - Agent id = island * island_size + slot; island id = y * cols + x on a rows x cols
+ *     torus.
+ *
+ * Canonical agent record (the device layout and the snapshot layout are the same):
+ *   int32 trait; uint32 counter; uint32 surface[W]; zero padding to record_bytes,
+ *   W = ceil(S*b/32), record_bytes = round_up(8 + 4W, 16).  Differentia of site k occupies
+ *   bits [k*b, k*b + b) of the surface, least-significant bit first, little-endian words.
+ *   Records are 16-byte aligned so each agent moves as whole 128-bit words.
+ */
+#ifndef GA_H
+#define GA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GA_OK 0
+#define GA_EINVAL (-1)       /* invalid argument or configuration                        */
+#define GA_ENOMEM (-2)       /* device allocation failed, or caller workspace too small  */
+#define GA_ECUDA (-3)        /* a CUDA runtime call or kernel launch failed              */
+#define GA_ETIMEOUT (-4)     /* a bounded device-side wait expired                       */
+#define GA_ESTATE (-5)       /* device state does not allow the request (e.g. counters of
+                                sampled agents differ, so no common rank table exists)   */
+#define GA_EUNSUPPORTED (-6) /* valid configuration with no compiled kernel for it       */
+#define GA_ERANGE (-7)       /* caller buffer too small                                  */
+
+/* Curation policy: which surface site the deposit of generation T overwrites. */
+#define GA_STEADY 0u /* evenly spaced retained ranks (gap <= 2T/S), any T                */
+#define GA_TILTED 1u /* recency-weighted: two ranks per hanoi level, S/2 levels           */
+#define GA_HYBRID 2u /* first S/2 sites steady on even ranks, last S/2 tilted on odd ranks */
+
+#define GA_SYNC 0u /* synchronous generations: deterministic, bit-exact                  */
+
+typedef struct ga_run ga_run;
+
+typedef struct ga_config {
+    uint32_t rows, cols;        /* torus of islands, each >= 1                                 */
+    uint32_t island_size;       /* N: power of two; GPU kernels exist for 4..128              */
+    uint32_t tournament_size;   /* n in [1, 8], draws with replacement (Sec. 2; Sec. 3 uses 5) */
+    double p_ben, p_del;        /* per-birth probabilities, p >= 0, p_ben + p_del <= 1        */
+    uint32_t surface_sites;     /* S: power of two, >= 4 (>= 8 for GA_HYBRID)                 */
+    uint32_t differentia_bits;  /* b in {1, 2, 4, 8}; S * b <= 256                            */
+    uint32_t curation;          /* GA_STEADY / GA_TILTED / GA_HYBRID                          */
+    uint32_t mode;              /* GA_SYNC                                                    */
+    uint64_t seed;              /* Philox key = (low 32 bits, high 32 bits)                   */
+    uint32_t run_id;            /* fourth Philox counter word: distinct runs draw disjointly  */
+    uint32_t reserved;          /* must be 0                                                  */
+    void *stream;               /* cudaStream_t for all of this run's GPU work (NULL: default) */
+} ga_config;
+
+/* Fill *cfg with the 32x32-torus defaults: N = 32, n = 5, p_ben = p_del = 0.01, S = 64,
+   b = 1, steady, sync, seed 42, run_id 0, default stream. */
+int ga_config_default(ga_config *cfg);
+
+/* Check a configuration without touching the GPU.  GA_EINVAL: invalid;
+   GA_EUNSUPPORTED: valid but no kernel is compiled for its island/record size. */
+int ga_config_check(const ga_config *cfg);
+
+/* Bytes of one canonical agent record for cfg (16, 32 or 48). */
+int ga_record_bytes(const ga_config *cfg, uint32_t *bytes);
+
+/* Bytes of device workspace a run of cfg needs (two population buffers plus a header). */
+int ga_workspace_bytes(const ga_config *cfg, size_t *bytes);
+
+/*
+ * Create a run and enqueue its founder initialisation (Sec. 2 "initialize"): every agent is
+ * a clone of one founder with trait 0, counter 0 and surface word w equal to word 0 of
+ * Philox4x32-10(counter (0, 0, w | 2 << 16, run_id), key seed).
+ * workspace: device pointer of at least ga_workspace_bytes() bytes, 256-byte aligned, owned
+ * by the caller; or NULL to let the library allocate (and later free) it.
+ * Errors: GA_EINVAL (config, alignment), GA_EUNSUPPORTED, GA_ENOMEM, GA_ECUDA.
+ */
+int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_run **out);
+
+/* Re-enqueue founder initialisation and set the generation counter to 0 (same effect as a
+   fresh ga_create with the same config).  Asynchronous. */
+int ga_reset(ga_run *run);
+
+/*
+ * Migration policy (Sec. 2): per_neighbor migrants arrive from each of the four neighbours
+ * on every generation g with g mod every_k == 0.  per_neighbor in {0, 1} (0 disables
+ * migration); every_k >= 1.  The default after ga_create is (1, 1).
+ */
+int ga_migrate_policy(ga_run *run, uint32_t per_neighbor, uint32_t every_k);
+
+/*
+ * Enqueue n_gens generations on the run's stream (Sec. 2 generational cycle, halting after
+ * n_gens).  Asynchronous; launch failures are returned here, nothing is read back.
+ * Generation g of a run always draws the same random numbers, so splitting n_gens over
+ * several calls gives bit-identical results.  Errors: GA_EINVAL (null run), GA_ECUDA.
+ */
+int ga_step(ga_run *run, uint32_t n_gens);
+
+/* Wait for the run's stream and report any error the device recorded. */
+int ga_sync(ga_run *run);
+
+/* Generations completed (enqueued) so far. */
+int ga_generation(const ga_run *run, uint64_t *generation);
+
+/* Kernels this run has launched so far (all of them the library's own). */
+int ga_launch_count(const ga_run *run, uint64_t *launches);
+
+/* Device pointer and size of the current population buffer (valid until the next
+   ga_step / ga_load / ga_destroy).  Read it only on the run's stream, or after ga_sync. */
+int ga_population(ga_run *run, void **device_ptr, size_t *bytes);
+
+/* Copy the whole population (canonical records, agent-id order) to host_dst.  Synchronous.
+   GA_ERANGE when cap is smaller than n_agents * record_bytes (*written gets the need). */
+int ga_snapshot(ga_run *run, void *host_dst, size_t cap, size_t *written);
+
+/* As ga_snapshot but into device memory, asynchronously on the run's stream. */
+int ga_snapshot_device(ga_run *run, void *device_dst, size_t cap, size_t *written);
+
+/* Replace the population with canonical records from host_src and set the generation
+   counter (checkpoint resume; bit-exact because draws are keyed by generation).  bytes
+   must equal n_agents * record_bytes.  Synchronous. */
+int ga_load(ga_run *run, const void *host_src, size_t bytes, uint64_t generation);
+
+/*
+ * Pairwise MRCA bounds (Fig. 1: post hoc relatedness from hstrat markers).
+ * agent_ids: n distinct agent ids (host); lo, hi: n(n-1)/2 uint32 each (host), pairs (i, j),
+ * i < j, in row-major upper-triangle order: pair index i*(2n-i-1)/2 + (j-i-1).
+ * All sampled agents must hold the same counter T (always true in GA_SYNC mode).  With the
+ * sites' retained ranks r_1 < ... < r_m (ranks < T) and i* the first index at which the
+ * two differentiae differ, the divergence rank D (first rank the two lineages drew in
+ * separate births) satisfies D in [lo, hi]:
+ *   hi = r_{i*} (certain), lo = r_{i*-K} + 1 or 0 if i* <= K; with no mismatch hi = T and
+ *   lo = r_{m-K+1} + 1 (0 if m < K); K = smallest integer with 2^(-bK) < 0.05, so lo holds
+ *   with confidence 0.95.
+ * Synchronous.  Scratch memory is allocated and freed on the run's stream.
+ * Errors: GA_EINVAL (n < 2, n > 65536, id out of range, null pointers), GA_ESTATE
+ * (counters differ), GA_ENOMEM, GA_ECUDA.
+ */
+int ga_mrca_bounds(ga_run *run, const uint32_t *agent_ids, uint32_t n, uint32_t *lo,
+                   uint32_t *hi);
+
+/* As ga_mrca_bounds with device buffers for ids, lo and hi; asynchronous on the run's
+   stream.  Ids are not range-checked on the host (the kernel skips out-of-range ids and
+   records GA_EINVAL, reported by ga_sync), counter mismatches are reported by ga_sync. */
+int ga_mrca_bounds_device(ga_run *run, const uint32_t *d_agent_ids, uint32_t n,
+                          uint32_t *d_lo, uint32_t *d_hi);
+
+/*
+ * Curation table: d_sites[i] = site that the deposit of rank t0 + i overwrites under the
+ * given policy over S sites, or -1 when that rank is not stored (hstrat update of Sec. 2;
+ * the policies are those of GA_STEADY / GA_TILTED / GA_HYBRID).  Computed by a kernel on
+ * `stream` (NULL: default stream), asynchronously.  Errors: GA_EINVAL (policy, S, or a
+ * range past 2^32 - 1), GA_ECUDA.
+ */
+int ga_curation_sites(uint32_t policy, uint32_t surface_sites, uint32_t t0, uint32_t count,
+                      int32_t *d_sites, void *stream);
+
+/* Destroy the run (synchronises its stream; frees library-owned memory). */
+int ga_destroy(ga_run *run);
+
+/* Static description of an error code. */
+const char *ga_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GA_H */

@@ -12,6 +12,7 @@ from .oracle import (  # noqa: F401
     HYBRID,
     philox4x32_10,
     site,
+    site_table,
     site_ranks,
     mrca_margin,
     mrca_bounds,

@@ -171,6 +171,12 @@ int64_t orc_site(uint32_t policy, uint32_t S, uint64_t T)
     }
 }
 
+/* Sites of ranks t0 .. t0 + count - 1, one call of orc_site each. */
+void orc_site_table(uint32_t policy, uint32_t S, uint64_t t0, uint64_t count, int64_t *out)
+{
+    for (uint64_t i = 0; i < count; ++i) out[i] = orc_site(policy, S, t0 + i);
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* The synchronous island GA.                                                            */
 /* ------------------------------------------------------------------------------------ */

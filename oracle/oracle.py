@@ -24,6 +24,8 @@ def _load():
     for name in ("orc_site_steady", "orc_site_tilted", "orc_site_hybrid"):
         getattr(lib, name).argtypes = [C.c_uint32, C.c_uint64]
         getattr(lib, name).restype = C.c_int64
+    lib.orc_site_table.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, i64p]
+    lib.orc_site_table.restype = None
     lib.orc_validate.argtypes = [C.c_void_p]
     lib.orc_validate.restype = C.c_int
     lib.orc_create.argtypes = [C.c_void_p]
@@ -89,6 +91,13 @@ def philox4x32_10(ctr, key):
 def site(policy, S, T):
     """Site that the deposit of rank T overwrites, or -1 when it is not stored."""
     return int(_load().orc_site(policy, S, T))
+
+
+def site_table(policy, S, t0, count):
+    """Sites of ranks t0 .. t0 + count - 1 as an int64 array (-1: not stored)."""
+    out = np.zeros(count, np.int64)
+    _load().orc_site_table(policy, S, t0, count, out.ctypes.data_as(C.POINTER(C.c_int64)))
+    return out
 
 
 def site_ranks(policy, S, T):

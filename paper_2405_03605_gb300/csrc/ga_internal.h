@@ -1,0 +1,51 @@
+// ga_internal.h -- host-side state of a run and the launchers shared by the library's
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "ga.h"
+
+struct ga_run {
+    ga_config cfg;
+    cudaStream_t stream;
+    uint32_t n_islands;
+    uint32_t n_agents;
+    uint32_t record_bytes;   // 16, 32 or 48
+    uint32_t surface_words;  // ceil(S*b/32)
+    uint32_t log2_sites;
+    uint32_t theta_ben, theta_del;
+    uint32_t per_neighbor, every_k;
+    uint64_t generation;
+    uint64_t launches;
+    void *workspace;
+    size_t workspace_bytes;
+    bool owns_workspace;
+    int *d_status;       // device error word (GA_OK or a GA_E* code), in the workspace header
+    uint8_t *pop[2];     // double-buffered population
+    int cur;             // index of the current population buffer
+};
+
+namespace ga {
+
+constexpr size_t kHeaderBytes = 256;
+
+// Largest number of generations one island-step launch runs without migration.
+constexpr uint32_t kMaxGensPerLaunch = 256;
+
+// island_step launch: generations [g0, g0 + n_gens) read from src, write dst; migration (if
+// `migrate`) happens only at g0.
+bool step_supported(uint32_t island_size, uint32_t surface_words);
+cudaError_t launch_founder(ga_run *run, void *dst);
+cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t g0,
+                               uint32_t n_gens, bool migrate);
+cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t *d_lo,
+                        uint32_t *d_hi, void *scratch);
+size_t mrca_scratch_bytes(const ga_run *run, uint32_t n);
+cudaError_t launch_curation_sites(uint32_t policy, uint32_t sites, uint32_t t0, uint32_t count,
+                                  int32_t *d_sites, cudaStream_t stream);
+
+}  // namespace ga

@@ -1,0 +1,218 @@
+// ga_mrca.cu -- pairwise MRCA bounds over sampled end-state agents (post hoc relatedness
+// estimation from hstrat markers, Fig. 1 caption of the paper).
+//
+// Pipeline (all on the run's stream):
+//   1. rank_kernel   : replay the curation rule over ranks 0..T-1; each site keeps the
+//                      largest rank that landed on it (atomicMax of rank + 1).
+//   2. order_kernel  : sort the occupied sites by rank (one block, S <= 256): r_1 < ... < r_m.
+//   3. pack_kernel   : gather each sampled agent's differentiae in rank order into a bit
+//                      string (differentia i at bits [i*b, i*b + b)), 8 words per agent.
+//   4. pair_kernel   : one warp per row i; for each j > i the first set bit of
+//                      packed[i] ^ packed[j] gives the first mismatching rank index i*,
+//                      from which hi = r_{i*} and lo = r_{i*-K} + 1 (0 if i* <= K); with no
+//                      mismatch hi = T, lo = r_{m-K+1} + 1 (0 if m < K).
+// The pair kernel is bound by its output: 8 bytes (lo, hi) per pair, written once with
+// streaming stores.
+#include "ga_device.cuh"
+#include "ga_internal.h"
+
+namespace ga {
+
+namespace {
+
+constexpr uint32_t kPackWords = 8;  // 256-bit rank-ordered strings
+constexpr int kPairThreads = 256;
+
+struct MrcaLayout {
+    uint32_t *holder;  // [S]  rank + 1 held by each site (0: none)
+    uint32_t *order;   // [S]  sites sorted by rank
+    uint32_t *ranks;   // [S]  sorted ranks
+    uint32_t *meta;    // [4]  m
+    uint32_t *packed;  // [n][kPackWords]
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+MrcaLayout carve(void *scratch, uint32_t S, uint32_t n)
+{
+    uint8_t *p = static_cast<uint8_t *>(scratch);
+    MrcaLayout l;
+    size_t off = 0;
+    l.holder = reinterpret_cast<uint32_t *>(p + off);
+    off = align_up(off + S * 4u, 256);
+    l.order = reinterpret_cast<uint32_t *>(p + off);
+    off = align_up(off + S * 4u, 256);
+    l.ranks = reinterpret_cast<uint32_t *>(p + off);
+    off = align_up(off + S * 4u, 256);
+    l.meta = reinterpret_cast<uint32_t *>(p + off);
+    off = align_up(off + 16u, 256);
+    l.packed = reinterpret_cast<uint32_t *>(p + off);
+    (void)n;
+    return l;
+}
+
+__global__ void rank_kernel(uint32_t *__restrict__ holder, uint32_t policy, uint32_t log2_sites,
+                            uint32_t sites, uint32_t T)
+{
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < T;
+         t += gridDim.x * blockDim.x) {
+        const int site = curation_site(policy, log2_sites, sites, t);
+        if (site >= 0) atomicMax(&holder[site], t + 1u);
+    }
+}
+
+__global__ void order_kernel(const uint32_t *__restrict__ holder, uint32_t *__restrict__ order,
+                             uint32_t *__restrict__ ranks, uint32_t *__restrict__ meta,
+                             uint32_t sites)
+{
+    __shared__ uint32_t h[256];
+    const uint32_t k = threadIdx.x;
+    const uint32_t mine = k < sites ? holder[k] : 0u;
+    h[k] = mine;
+    const int m = __syncthreads_count(mine != 0u);
+    if (mine != 0u) {
+        uint32_t pos = 0;
+        for (uint32_t q = 0; q < sites; ++q) pos += (h[q] != 0u && h[q] < mine) ? 1u : 0u;
+        order[pos] = k;
+        ranks[pos] = mine - 1u;
+    }
+    if (k == 0) meta[0] = static_cast<uint32_t>(m);
+}
+
+__global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_words,
+                            uint32_t n_agents, const uint32_t *__restrict__ ids, uint32_t n,
+                            const uint32_t *__restrict__ order, const uint32_t *__restrict__ meta,
+                            uint32_t bits, uint32_t T, uint32_t *__restrict__ packed,
+                            int *__restrict__ status)
+{
+    __shared__ uint32_t ord[256];
+    const uint32_t m = meta[0];
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ord[i] = order[i];
+    __syncthreads();
+    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    uint32_t out[kPackWords] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint32_t id = ids[a];
+    if (id >= n_agents) {
+        atomicCAS(status, GA_OK, GA_EINVAL);
+    } else {
+        const uint32_t *rec = pop + static_cast<size_t>(id) * record_words;
+        if (rec[1] != T) atomicCAS(status, GA_OK, GA_ESTATE);
+        uint32_t surf[kPackWords];
+#pragma unroll
+        for (uint32_t w = 0; w < kPackWords; ++w) surf[w] = (2u + w < record_words) ? rec[2 + w] : 0u;
+        const uint32_t mask = (1u << bits) - 1u;
+        for (uint32_t i = 0; i < m; ++i) {
+            const uint32_t pos = ord[i] * bits;
+            uint32_t word = 0;
+#pragma unroll
+            for (uint32_t w = 0; w < kPackWords; ++w)
+                if (w == (pos >> 5)) word = surf[w];
+            const uint32_t d = (word >> (pos & 31u)) & mask;
+            const uint32_t dst = i * bits;
+#pragma unroll
+            for (uint32_t w = 0; w < kPackWords; ++w)
+                if (w == (dst >> 5)) out[w] |= d << (dst & 31u);
+        }
+    }
+    uint4 *o = reinterpret_cast<uint4 *>(packed + static_cast<size_t>(a) * kPackWords);
+    o[0] = make_uint4(out[0], out[1], out[2], out[3]);
+    o[1] = make_uint4(out[4], out[5], out[6], out[7]);
+}
+
+__global__ void __launch_bounds__(kPairThreads)
+pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__restrict__ ranks_g,
+            const uint32_t *__restrict__ meta, uint32_t bits, uint32_t K, uint32_t T,
+            uint32_t *__restrict__ lo, uint32_t *__restrict__ hi)
+{
+    __shared__ uint32_t ranks[256];
+    const uint32_t m = meta[0];
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ranks[i] = ranks_g[i];
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= n) return;
+    const uint32_t pw = (m * bits + 31u) >> 5;
+    uint32_t mine[kPackWords];
+    const uint4 *pi = reinterpret_cast<const uint4 *>(packed + static_cast<size_t>(row) * kPackWords);
+    const uint4 a0 = pi[0], a1 = pi[1];
+    mine[0] = a0.x; mine[1] = a0.y; mine[2] = a0.z; mine[3] = a0.w;
+    mine[4] = a1.x; mine[5] = a1.y; mine[6] = a1.z; mine[7] = a1.w;
+    const uint32_t none_hi = T;
+    const uint32_t none_lo = m >= K ? ranks[m - K] + 1u : 0u;
+    const size_t base = static_cast<size_t>(row) * (2ull * n - row - 1ull) / 2ull;
+    for (uint32_t j = row + 1u + lane; j < n; j += 32u) {
+        const uint4 *pj = reinterpret_cast<const uint4 *>(packed + static_cast<size_t>(j) * kPackWords);
+        const uint4 b0 = __ldg(&pj[0]);
+        uint32_t x[kPackWords];
+        x[0] = b0.x ^ mine[0]; x[1] = b0.y ^ mine[1]; x[2] = b0.z ^ mine[2]; x[3] = b0.w ^ mine[3];
+        if (pw > 4u) {
+            const uint4 b1 = __ldg(&pj[1]);
+            x[4] = b1.x ^ mine[4]; x[5] = b1.y ^ mine[5]; x[6] = b1.z ^ mine[6]; x[7] = b1.w ^ mine[7];
+        } else {
+            x[4] = x[5] = x[6] = x[7] = 0u;
+        }
+        uint32_t first_bit = 0xFFFFFFFFu;
+#pragma unroll
+        for (int w = kPackWords - 1; w >= 0; --w)
+            if (x[w] != 0u) first_bit = 32u * w + (__ffs(x[w]) - 1u);
+        uint32_t l, h;
+        if (first_bit == 0xFFFFFFFFu) {
+            h = none_hi;
+            l = none_lo;
+        } else {
+            const uint32_t istar = first_bit / bits;  // 0-based index of the first mismatch
+            h = ranks[istar];
+            l = istar >= K ? ranks[istar - K] + 1u : 0u;
+        }
+        const size_t p = base + (j - row - 1u);
+        __stcs(&lo[p], l);
+        __stcs(&hi[p], h);
+    }
+}
+
+uint32_t margin(uint32_t bits)
+{
+    // smallest K with 2^(-bits*K) < 0.05, i.e. bits*K > log2(20) = 4.32
+    uint32_t K = 1;
+    while (bits * K <= 4u) ++K;
+    return K;
+}
+
+}  // namespace
+
+size_t mrca_scratch_bytes(const ga_run *run, uint32_t n)
+{
+    const size_t S = run->cfg.surface_sites;
+    return 3 * align_up(S * 4, 256) + 256 + static_cast<size_t>(n) * kPackWords * 4 + 256;
+}
+
+cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t *d_lo,
+                        uint32_t *d_hi, void *scratch)
+{
+    const uint32_t S = run->cfg.surface_sites, b = run->cfg.differentia_bits;
+    const uint32_t T = static_cast<uint32_t>(run->generation);
+    MrcaLayout l = carve(scratch, S, n);
+    cudaError_t e = cudaMemsetAsync(l.holder, 0, S * sizeof(uint32_t), run->stream);
+    if (e != cudaSuccess) return e;
+    if (T > 0) {
+        uint32_t blocks = (T + 255u) / 256u;
+        if (blocks > 4096u) blocks = 4096u;
+        rank_kernel<<<blocks, 256, 0, run->stream>>>(l.holder, run->cfg.curation,
+                                                     run->log2_sites, S, T);
+        run->launches += 1;
+    }
+    order_kernel<<<1, 256, 0, run->stream>>>(l.holder, l.order, l.ranks, l.meta, S);
+    run->launches += 1;
+    pack_kernel<<<(n + 127u) / 128u, 128, 0, run->stream>>>(
+        reinterpret_cast<const uint32_t *>(run->pop[run->cur]), run->record_bytes / 4u,
+        run->n_agents, d_ids, n, l.order, l.meta, b, T, l.packed, run->d_status);
+    run->launches += 1;
+    const uint32_t rows_per_block = kPairThreads / 32;
+    pair_kernel<<<(n + rows_per_block - 1) / rows_per_block, kPairThreads, 0, run->stream>>>(
+        l.packed, n, l.ranks, l.meta, b, margin(b), T, d_lo, d_hi);
+    run->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace ga

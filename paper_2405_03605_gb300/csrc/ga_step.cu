@@ -1,0 +1,361 @@
+// ga_step.cu -- founder initialisation and the fused island-step kernel.
+//
+// One generation (Sec. 2 of the paper, in its order): migration (when due), evaluation
+// (fitness = trait), tournament selection of every next-generation slot, copy and mutation
+// of the child, and the hstrat deposit for the elapsed generation.
+//
+// Mapping: one island per warp for N >= 32 (N/32 agents per lane), 32/N islands per warp
+// for N < 32 (one agent per lane, shuffles of width N).  Each lane keeps its agents'
+// records in registers; tournaments read candidate traits and copy the winner's record
+// with __shfl_sync, so an island never leaves the register file between the launch's
+// first load and last store.  A launch runs generations [g0, g0 + n) with migration only at
+// g0: the population is read once from `src` and written once to `dst` per launch, and
+// immigrants are read straight from the neighbours' records in `src` (the whole previous
+// population doubles as the migration halo, so no separate halo buffer or grid barrier is
+// needed and the result does not depend on launch order).
+#include "ga_device.cuh"
+#include "ga_internal.h"
+
+namespace ga {
+
+constexpr int kStepThreads = 256;
+
+struct StepArgs {
+    const uint4 *__restrict__ src;
+    uint4 *__restrict__ dst;
+    uint32_t rows, cols, n_islands;
+    uint32_t tsize;
+    uint32_t theta_ben, theta_del;
+    uint32_t policy, log2_sites, sites, bits;
+    Key key;
+    uint32_t run_id;
+    uint32_t g0, n_gens, migrate;
+};
+
+// Candidate trait of slot idx of this lane's island.
+template <int N, int A, int SEG>
+__device__ __forceinline__ int candidate_trait(unsigned mask, const int (&trait)[A], uint32_t idx)
+{
+    if constexpr (N <= 32) {
+        return __shfl_sync(mask, trait[0], static_cast<int>(idx), SEG);
+    } else {
+        int t = 0;
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            const int x = __shfl_sync(mask, trait[q], static_cast<int>(idx & 31u));
+            if ((idx >> 5) == static_cast<uint32_t>(q)) t = x;
+        }
+        return t;
+    }
+}
+
+// N: island size; SW: surface words carried per record (the record is RW words).
+template <int N, int SW>
+__global__ void __launch_bounds__(kStepThreads) island_step_kernel(const StepArgs p)
+{
+    constexpr int A = N >= 32 ? N / 32 : 1;      // agents per lane
+    constexpr int P = N >= 32 ? 1 : 32 / N;      // islands per warp
+    constexpr int SEG = N >= 32 ? 32 : N;        // lanes per island
+    constexpr int LW = 2 + SW;                   // live words: trait, counter, surface
+    constexpr int RW = (LW + 3) / 4 * 4;         // record words
+    constexpr int Q = RW / 4;                    // 128-bit words per record
+
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t island = warp * P + lane / SEG;
+    const bool valid = island < p.n_islands;
+    const unsigned mask = __ballot_sync(0xffffffffu, valid);
+    if (!valid) return;
+    const uint32_t seg_lane = lane % SEG;
+
+    uint32_t rec[A][LW];
+#pragma unroll
+    for (int ag = 0; ag < A; ++ag) {
+        const uint32_t agent = island * N + seg_lane + 32u * ag;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const uint4 v = __ldg(&p.src[static_cast<size_t>(agent) * Q + q]);
+            const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (4 * q + e < LW) rec[ag][4 * q + e] = w4[e];
+        }
+    }
+
+    for (uint32_t it = 0; it < p.n_gens; ++it) {
+        const uint32_t g = p.g0 + it;
+
+        // birth draws of this lane's child slots: (B0, B1) tournament bytes, B2 mutation,
+        // B3 differentia (low bits) and, for slots 0..3, migration bits 8..31
+        uint4 w[A];
+#pragma unroll
+        for (int ag = 0; ag < A; ++ag)
+            w[ag] = philox(g, island, (seg_lane + 32u * ag) | (kBirth << 16), p.run_id, p.key);
+
+        if (it == 0 && p.migrate) {
+            // migration words of directions N, S, E, W come from slots 0..3
+            uint32_t u[4];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) u[d] = __shfl_sync(mask, w[0].w, d, SEG);
+            // four distinct landing slots: partial Fisher-Yates over [0, N) in direction
+            // order; entry e records "position r[e] now holds value v[e]" (later wins)
+            uint32_t r[4], v[4], slot[4];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                r[d] = d + (((u[d] >> 16) * static_cast<uint32_t>(N - d)) >> 16);
+                uint32_t vd = d, vr = r[d];
+#pragma unroll
+                for (int e = 0; e < d; ++e) {
+                    if (r[e] == static_cast<uint32_t>(d)) vd = v[e];
+                    if (r[e] == r[d]) vr = v[e];
+                }
+                slot[d] = vr;
+                v[d] = vd;
+            }
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                const uint32_t from = torus_neighbour(island, d, p.rows, p.cols);
+                const uint32_t e = (((u[d] >> 8) & 0xFFu) * N) >> 8;
+                const uint4 *srec = p.src + (static_cast<size_t>(from) * N + e) * Q;
+#pragma unroll
+                for (int ag = 0; ag < A; ++ag) {
+                    if (seg_lane + 32u * ag == slot[d]) {
+#pragma unroll
+                        for (int q = 0; q < Q; ++q) {
+                            const uint4 x = __ldg(&srec[q]);
+                            const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (4 * q + k < LW) rec[ag][4 * q + k] = w4[k];
+                        }
+                    }
+                }
+            }
+        }
+
+        // evaluation + tournament: best of n draws with replacement, earliest wins ties
+        int trait[A];
+#pragma unroll
+        for (int ag = 0; ag < A; ++ag) trait[ag] = static_cast<int>(rec[ag][0]);
+        uint32_t win[A];
+#pragma unroll
+        for (int ag = 0; ag < A; ++ag) {
+            uint32_t best = 0;
+            int best_trait = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (static_cast<uint32_t>(i) < p.tsize) {
+                    const uint32_t word = i < 4 ? w[ag].x : w[ag].y;
+                    const uint32_t idx = (((word >> (8 * (i & 3))) & 0xFFu) * N) >> 8;
+                    const int t = candidate_trait<N, A, SEG>(mask, trait, idx);
+                    if (i == 0 || t > best_trait) {
+                        best = idx;
+                        best_trait = t;
+                    }
+                }
+            }
+            win[ag] = best;
+        }
+
+        // copy the winner's record
+        uint32_t child[A][LW];
+#pragma unroll
+        for (int ag = 0; ag < A; ++ag) {
+#pragma unroll
+            for (int k = 0; k < LW; ++k) {
+                if constexpr (N <= 32) {
+                    child[ag][k] = __shfl_sync(mask, rec[0][k], static_cast<int>(win[ag]), SEG);
+                } else {
+                    uint32_t val = 0;
+#pragma unroll
+                    for (int q = 0; q < A; ++q) {
+                        const uint32_t x =
+                            __shfl_sync(mask, rec[q][k], static_cast<int>(win[ag] & 31u));
+                        if ((win[ag] >> 5) == static_cast<uint32_t>(q)) val = x;
+                    }
+                    child[ag][k] = val;
+                }
+            }
+        }
+
+        // mutation and hstrat deposit
+#pragma unroll
+        for (int ag = 0; ag < A; ++ag) {
+            const uint32_t x = w[ag].z;
+            uint32_t t = child[ag][0];
+            if (x < p.theta_del) t -= 1u;
+            else if (x - p.theta_del < p.theta_ben) t += 1u;
+            child[ag][0] = t;
+
+            const uint32_t c = child[ag][1];
+            const int site = curation_site(p.policy, p.log2_sites, p.sites, c);
+            if (site >= 0) {
+                const uint32_t pos = static_cast<uint32_t>(site) * p.bits;
+                const uint32_t wi = pos >> 5, sh = pos & 31u;
+                const uint32_t m = ((1u << p.bits) - 1u) << sh;
+                const uint32_t val = (w[ag].w << sh) & m;
+#pragma unroll
+                for (int k = 0; k < SW; ++k)
+                    if (static_cast<uint32_t>(k) == wi) child[ag][2 + k] = (child[ag][2 + k] & ~m) | val;
+            }
+            child[ag][1] = c + 1u;
+#pragma unroll
+            for (int k = 0; k < LW; ++k) rec[ag][k] = child[ag][k];
+        }
+    }
+
+#pragma unroll
+    for (int ag = 0; ag < A; ++ag) {
+        const uint32_t agent = island * N + seg_lane + 32u * ag;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) w4[e] = (4 * q + e < LW) ? rec[ag][4 * q + e] : 0u;
+            p.dst[static_cast<size_t>(agent) * Q + q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+    }
+}
+
+// Every record becomes the founder: trait 0, counter 0, surface word w = word 0 of
+// Philox((0, 0, w | FOUNDER << 16, run_id)); surface bits past S*b are zero.
+__global__ void founder_kernel(uint4 *__restrict__ dst, uint32_t n_agents, uint32_t q_per_rec,
+                               uint32_t surface_words, uint32_t top_bits, Key key,
+                               uint32_t run_id)
+{
+    __shared__ uint32_t words[12];
+    if (threadIdx.x < 12) {
+        uint32_t val = 0u;
+        const uint32_t k = threadIdx.x;
+        if (k >= 2 && k - 2 < surface_words) {
+            val = philox(0u, 0u, (k - 2) | (kFounder << 16), run_id, key).x;
+            if (k - 2 == surface_words - 1 && top_bits) val &= (1u << top_bits) - 1u;
+        }
+        words[k] = val;
+    }
+    __syncthreads();
+    const size_t total = static_cast<size_t>(n_agents) * q_per_rec;
+    for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const uint32_t q = static_cast<uint32_t>(i % q_per_rec);
+        dst[i] = make_uint4(words[4 * q], words[4 * q + 1], words[4 * q + 2], words[4 * q + 3]);
+    }
+}
+
+__global__ void curation_sites_kernel(uint32_t policy, uint32_t log2_sites, uint32_t sites,
+                                      uint32_t t0, uint32_t count, int32_t *__restrict__ out)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += gridDim.x * blockDim.x)
+        out[i] = curation_site(policy, log2_sites, sites, t0 + i);
+}
+
+namespace {
+
+using StepKernel = void (*)(StepArgs);
+
+// The template's surface-word count fills the record: 16-byte records carry 2 surface words,
+// 32-byte records 6 and 48-byte records 8 (words past the run's own S*b bits are zero).
+template <int N>
+StepKernel pick_sw(uint32_t surface_words)
+{
+    if (surface_words <= 2) return island_step_kernel<N, 2>;
+    if (surface_words <= 6) return island_step_kernel<N, 6>;
+    if (surface_words <= 8) return island_step_kernel<N, 8>;
+    return nullptr;
+}
+
+StepKernel pick_kernel(uint32_t island_size, uint32_t surface_words)
+{
+    switch (island_size) {
+    case 4: return pick_sw<4>(surface_words);
+    case 8: return pick_sw<8>(surface_words);
+    case 16: return pick_sw<16>(surface_words);
+    case 32: return pick_sw<32>(surface_words);
+    case 64: return pick_sw<64>(surface_words);
+    case 128: return pick_sw<128>(surface_words);
+    default: return nullptr;
+    }
+}
+
+uint32_t sm_count()
+{
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return static_cast<uint32_t>(sms);
+}
+
+}  // namespace
+
+bool step_supported(uint32_t island_size, uint32_t surface_words)
+{
+    return pick_kernel(island_size, surface_words) != nullptr;
+}
+
+cudaError_t launch_founder(ga_run *run, void *dst)
+{
+    const uint32_t q = run->record_bytes / 16;
+    const uint32_t top = (run->cfg.surface_sites * run->cfg.differentia_bits) % 32u;
+    const Key key{static_cast<uint32_t>(run->cfg.seed), static_cast<uint32_t>(run->cfg.seed >> 32)};
+    const size_t total = static_cast<size_t>(run->n_agents) * q;
+    size_t blocks = (total + 255) / 256;
+    const size_t cap = static_cast<size_t>(sm_count()) * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    founder_kernel<<<static_cast<unsigned>(blocks), 256, 0, run->stream>>>(
+        static_cast<uint4 *>(dst), run->n_agents, q, run->surface_words, top, key, run->cfg.run_id);
+    run->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t g0,
+                               uint32_t n_gens, bool migrate)
+{
+    const StepKernel k = pick_kernel(run->cfg.island_size, run->surface_words);
+    if (!k) return cudaErrorInvalidValue;
+    StepArgs a;
+    a.src = static_cast<const uint4 *>(src);
+    a.dst = static_cast<uint4 *>(dst);
+    a.rows = run->cfg.rows;
+    a.cols = run->cfg.cols;
+    a.n_islands = run->n_islands;
+    a.tsize = run->cfg.tournament_size;
+    a.theta_ben = run->theta_ben;
+    a.theta_del = run->theta_del;
+    a.policy = run->cfg.curation;
+    a.log2_sites = run->log2_sites;
+    a.sites = run->cfg.surface_sites;
+    a.bits = run->cfg.differentia_bits;
+    a.key = Key{static_cast<uint32_t>(run->cfg.seed), static_cast<uint32_t>(run->cfg.seed >> 32)};
+    a.run_id = run->cfg.run_id;
+    a.g0 = g0;
+    a.n_gens = n_gens;
+    a.migrate = migrate ? 1u : 0u;
+    const uint32_t N = run->cfg.island_size;
+    const uint32_t islands_per_warp = N >= 32 ? 1u : 32u / N;
+    const uint32_t warps = (run->n_islands + islands_per_warp - 1) / islands_per_warp;
+    const uint32_t warps_per_block = kStepThreads / 32;
+    const uint32_t blocks = (warps + warps_per_block - 1) / warps_per_block;
+    k<<<blocks, kStepThreads, 0, run->stream>>>(a);
+    run->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_curation_sites(uint32_t policy, uint32_t sites, uint32_t t0, uint32_t count,
+                                  int32_t *d_sites, cudaStream_t stream)
+{
+    if (count == 0) return cudaSuccess;
+    uint32_t s = 0;
+    while ((1u << s) < sites) ++s;
+    uint32_t blocks = (count + 255u) / 256u;
+    if (blocks > 8192u) blocks = 8192u;
+    curation_sites_kernel<<<blocks, 256, 0, stream>>>(policy, s, sites, t0, count, d_sites);
+    return cudaGetLastError();
+}
+
+}  // namespace ga

@@ -1,0 +1,93 @@
+"""The C-ABI library builds, loads and exports every entry point include/ga.h declares; host-only
+calls (configuration checks and sizes) work without a GPU."""
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2405_03605_gb300 import build, ga
+    build.build()
+    return ga.load_library()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "ga.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ga_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_exported(lib):
+    from paper_2405_03605_gb300 import ga
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(ga.EXPORTED)
+
+
+def test_config_checks(lib):
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import SMALL_TORUS, variant_shapes, PAPER_ADAPTIVE
+    assert ga.config_check(SMALL_TORUS) == 0
+    assert ga.config_check(PAPER_ADAPTIVE) == 0
+    for n in (16, 32, 64):
+        for shape in variant_shapes(n).values():
+            assert ga.config_check(shape) == 0
+    assert ga.config_check(SMALL_TORUS.with_(island_size=24)) == -1
+    assert ga.config_check(SMALL_TORUS.with_(tournament_size=0)) == -1
+    assert ga.config_check(SMALL_TORUS.with_(tournament_size=9)) == -1
+    assert ga.config_check(SMALL_TORUS.with_(p_ben=0.6, p_del=0.5)) == -1
+    assert ga.config_check(SMALL_TORUS.with_(differentia_bits=3)) == -1
+    assert ga.config_check(SMALL_TORUS.with_(surface_sites=512)) == -1
+    assert ga.config_check(SMALL_TORUS.with_(surface_sites=4, curation=2)) == -1
+    assert ga.config_check(SMALL_TORUS.with_(rows=0)) == -1
+    # valid but no kernel compiled for 256-agent islands
+    assert ga.config_check(SMALL_TORUS.with_(island_size=256)) == -6
+
+
+def test_sizes(lib):
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import SMALL_TORUS, variant_shapes, PAPER_ADAPTIVE
+    assert ga.record_bytes(SMALL_TORUS) == 16
+    v = variant_shapes(32)
+    assert ga.record_bytes(v["steady256x1"]) == 48
+    assert ga.record_bytes(v["tilted32x8"]) == 48
+    assert ga.record_bytes(v["hybrid64x1"]) == 16
+    assert ga.record_bytes(SMALL_TORUS.with_(surface_sites=128)) == 32
+    n = PAPER_ADAPTIVE.n_agents
+    assert n == 16777216
+    assert ga.workspace_bytes(PAPER_ADAPTIVE) == 256 + 2 * n * 16
+
+
+def test_strerror(lib):
+    from paper_2405_03605_gb300 import ga
+    assert ga.strerror(0) == "ok"
+    assert "invalid" in ga.strerror(-1)
+    assert ga.strerror(-99) == "unknown error"
+
+
+def test_record_layout_matches_oracle(lib):
+    import oracle
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import SMALL_TORUS
+    for S, b in ((64, 1), (256, 1), (32, 8), (128, 1), (16, 2), (4, 1)):
+        assert ga.record_bytes(SMALL_TORUS.with_(surface_sites=S, differentia_bits=b)) == \
+            oracle.record_bytes(S, b)
+
+
+def test_product_path_has_no_oracle_reference():
+    """The library and its binding never load the CPU oracle."""
+    pkg = os.path.join(ROOT, "paper_2405_03605_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                with open(os.path.join(dirpath, fn)) as f:
+                    text = f.read()
+                assert "import oracle" not in text and "from oracle" not in text, fn
+                assert "ga_oracle" not in text and "orc_" not in text, fn

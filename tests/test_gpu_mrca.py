@@ -1,0 +1,64 @@
+"""GPU MRCA-bound kernels versus the oracle, exact on every (lo, hi) pair."""
+import numpy as np
+import pytest
+
+from gpu_util import gpu_run, oracle_for
+from paper_2405_03605_gb300.workloads import RunShape, SMALL_TORUS, variant_shapes, \
+    sample_agent_ids
+
+pytestmark = pytest.mark.gpu
+
+
+def both(shape, gens, n_ids, seed=1):
+    g = gpu_run(shape)
+    g.step(gens)
+    g.sync()
+    o = oracle_for(shape)
+    o.step(gens)
+    ids = sample_agent_ids(shape.n_agents, n_ids, seed=seed)
+    return g, o, ids
+
+
+@pytest.mark.parametrize("gens", [0, 1, 5, 63, 64, 65, 1000])
+def test_small_torus_pairs(gens):
+    g, o, ids = both(SMALL_TORUS, gens, 700)
+    lo, hi = g.mrca_bounds(ids)
+    elo, ehi = o.mrca_bounds(ids)
+    assert np.array_equal(lo, elo)
+    assert np.array_equal(hi, ehi)
+    assert (lo <= hi).all() and (hi <= gens).all()
+
+
+@pytest.mark.parametrize("name", ["steady256x1", "tilted32x8", "hybrid64x1"])
+def test_variant_pairs(name):
+    shape = variant_shapes(32)[name].with_(rows=6, cols=8)
+    g, o, ids = both(shape, 700, 500, seed=3)
+    lo, hi = g.mrca_bounds(ids)
+    elo, ehi = o.mrca_bounds(ids)
+    assert np.array_equal(lo, elo)
+    assert np.array_equal(hi, ehi)
+
+
+def test_device_entry_point_matches_host():
+    import torch
+    shape = RunShape(rows=8, cols=8, seed=9)
+    g, o, ids = both(shape, 200, 333)
+    d_ids = torch.from_numpy(ids.view(np.int32)).cuda()
+    lo, hi = g.mrca_bounds_device(d_ids)
+    g.sync()
+    hlo, hhi = g.mrca_bounds(ids)
+    assert np.array_equal(lo.cpu().numpy().view(np.uint32), hlo)
+    assert np.array_equal(hi.cpu().numpy().view(np.uint32), hhi)
+
+
+def test_two_samples_and_errors():
+    from paper_2405_03605_gb300 import ga
+    shape = RunShape(rows=2, cols=2, seed=2)
+    g, o, _ = both(shape, 30, 2)
+    lo, hi = g.mrca_bounds(np.array([3, 100], np.uint32))
+    elo, ehi = o.mrca_bounds(np.array([3, 100], np.uint32))
+    assert (lo[0], hi[0]) == (elo[0], ehi[0])
+    with pytest.raises(ga.GaError):
+        g.mrca_bounds(np.array([0, shape.n_agents], np.uint32))
+    with pytest.raises(ga.GaError):
+        g.mrca_bounds(np.array([0], np.uint32))

@@ -93,6 +93,11 @@ class Clocks:
         self.gpu = gpu_index
         if shutil.which("nvidia-smi") is None:
             return
+        visible = os.environ.get("CUDA_VISIBLE_DEVICES", "").strip()
+        if visible:
+            ids = [x.strip() for x in visible.split(",") if x.strip()]
+            if gpu_index < len(ids):
+                gpu_index = ids[gpu_index]
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         self.f = open(self.path, "w")

@@ -177,6 +177,36 @@ int ga_mrca_bounds_device(ga_run *run, const uint32_t *d_agent_ids, uint32_t n,
 int ga_curation_sites(uint32_t policy, uint32_t surface_sites, uint32_t t0, uint32_t count,
                       int32_t *d_sites, void *stream);
 
+/*
+ * ga_mrca_bounds without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- for instance a process
+ * whose framework has already reserved the GPU's memory for its own caching allocator (so
+ * cudaMalloc fails), a plugin or callback that its host forbids from allocating, or a
+ * latency-critical path that cannot afford cudaMalloc/cudaFree, which may synchronise the
+ * device.  It computes exactly what ga_mrca_bounds_device computes, from caller-owned
+ * device buffers and without a ga_run:
+ *   d_records      canonical records of n_agents agents (16-byte aligned device memory),
+ *                  record_bytes = round_up(8 + 4 ceil(S b / 32), 16);
+ *   curation, surface_sites, differentia_bits: the run's GA_STEADY/TILTED/HYBRID, S, b;
+ *   generation     T, the counter every sampled agent must hold;
+ *   d_agent_ids    n device uint32 ids, 2 <= n <= 4096 (larger n: GA_EINVAL);
+ *   d_lo, d_hi     n(n-1)/2 device uint32 each, pairs in row-major upper-triangle order.
+ * Its scratch (about 135 KB) is a fixed array inside the library's device image, which
+ * every GPU that loads the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress, with the device
+ * current); make that first call before any stream capture.  All calls on a device share
+ * the one array and each call overwrites it, so calls that overlap on the GPU (from several
+ * host threads or streams at once) race and must be serialised by the caller.
+ * Synchronous: enqueues on `stream` (NULL: default stream), waits for it, and returns
+ * GA_ESTATE when an agent's counter differs from T, GA_EINVAL for an id >= n_agents,
+ * GA_EINVAL for invalid arguments, GA_ECUDA for runtime failures.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ */
+int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_bytes, uint32_t n_agents,
+                           uint32_t curation, uint32_t surface_sites, uint32_t differentia_bits,
+                           uint32_t generation, const uint32_t *d_agent_ids, uint32_t n,
+                           uint32_t *d_lo, uint32_t *d_hi, void *stream);
+
 /* Destroy the run (synchronises its stream; frees library-owned memory). */
 int ga_destroy(ga_run *run);
 

@@ -13,6 +13,8 @@
 //                      mismatch hi = T, lo = r_{m-K+1} + 1 (0 if m < K).
 // The pair kernel is bound by its output: 8 bytes (lo, hi) per pair, written once with
 // streaming stores.
+#include <mutex>
+
 #include "ga_device.cuh"
 #include "ga_internal.h"
 
@@ -216,3 +218,105 @@ cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t
 }
 
 }  // namespace ga
+
+// ---------------------------------------------------------------------------------------
+// ga_mrca_bounds_noalloc: the same four MRCA kernels with their scratch held in a fixed
+// device array instead of memory allocated per call, for callers that cannot allocate
+// device memory (see include/ga.h).
+//
+// The array is a file-scope __device__ variable, so every GPU that loads this library holds
+// its own copy until the process exits.  In host code the name g_mrca_fixed_scratch is only
+// a host-side stand-in for the symbol; its device address comes from cudaGetSymbolAddress,
+// taken once per device (with that device current) on the first call made on that device.
+// Every call on a device reuses the same array: the status word and the site-rank table are
+// cleared at the start of each call, the rest is fully rewritten before it is read.
+// ---------------------------------------------------------------------------------------
+namespace ga {
+namespace {
+
+constexpr uint32_t kFixedMaxSample = 4096;    // largest n accepted
+constexpr uint32_t kFixedMaxSites = 256;      // S * b <= 256 bits
+constexpr size_t kFixedStatusBytes = 256;     // device status word, padded
+// status, then the same layout carve() gives the per-call scratch, sized for S = 256, n = 4096
+constexpr size_t kFixedScratchBytes =
+    kFixedStatusBytes + 3 * 1024 + 256 + static_cast<size_t>(kFixedMaxSample) * kPackWords * 4 + 256;
+
+static __device__ __align__(256) unsigned char g_mrca_fixed_scratch[kFixedScratchBytes];
+
+std::mutex g_fixed_mutex;
+constexpr int kMaxDevices = 64;
+void *g_fixed_address[kMaxDevices] = {};
+
+// Device address of the fixed scratch for the current device (looked up once per device).
+int fixed_scratch_address(void **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GA_ECUDA;
+    std::lock_guard<std::mutex> lock(g_fixed_mutex);
+    if (g_fixed_address[dev] == nullptr) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_mrca_fixed_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return GA_ECUDA;
+        }
+        g_fixed_address[dev] = p;
+    }
+    *out = g_fixed_address[dev];
+    return GA_OK;
+}
+
+}  // namespace
+
+}  // namespace ga
+
+extern "C" int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_bytes,
+                                      uint32_t n_agents, uint32_t curation,
+                                      uint32_t surface_sites, uint32_t differentia_bits,
+                                      uint32_t generation, const uint32_t *d_agent_ids,
+                                      uint32_t n, uint32_t *d_lo, uint32_t *d_hi, void *stream)
+{
+    using namespace ga;
+    const uint32_t S = surface_sites, b = differentia_bits;
+    if (!d_records || !d_agent_ids || !d_lo || !d_hi) return GA_EINVAL;
+    if (n < 2 || n > kFixedMaxSample) return GA_EINVAL;
+    if (curation > GA_HYBRID) return GA_EINVAL;
+    if (S == 0u || (S & (S - 1u)) != 0u || S < (curation == GA_HYBRID ? 8u : 4u)) return GA_EINVAL;
+    if (!(b == 1u || b == 2u || b == 4u || b == 8u) || S * b > kFixedMaxSites) return GA_EINVAL;
+    const uint32_t words = (S * b + 31u) / 32u;
+    if (record_bytes != (8u + 4u * words + 15u) / 16u * 16u || n_agents == 0u) return GA_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_records) % 16u != 0u) return GA_EINVAL;
+
+    void *base = nullptr;
+    int rc = fixed_scratch_address(&base);
+    if (rc != GA_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *status = static_cast<int *>(base);
+    MrcaLayout l = carve(static_cast<uint8_t *>(base) + kFixedStatusBytes, S, n);
+    uint32_t log2_sites = 0;
+    while ((1u << log2_sites) < S) ++log2_sites;
+
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess ||
+        cudaMemsetAsync(l.holder, 0, S * sizeof(uint32_t), st) != cudaSuccess)
+        return GA_ECUDA;
+    if (generation > 0u) {
+        uint32_t blocks = (generation + 255u) / 256u;
+        if (blocks > 4096u) blocks = 4096u;
+        rank_kernel<<<blocks, 256, 0, st>>>(l.holder, curation, log2_sites, S, generation);
+    }
+    order_kernel<<<1, 256, 0, st>>>(l.holder, l.order, l.ranks, l.meta, S);
+    pack_kernel<<<(n + 127u) / 128u, 128, 0, st>>>(static_cast<const uint32_t *>(d_records),
+                                                   record_bytes / 4u, n_agents, d_agent_ids, n,
+                                                   l.order, l.meta, b, generation, l.packed,
+                                                   status);
+    const uint32_t rows_per_block = kPairThreads / 32;
+    pair_kernel<<<(n + rows_per_block - 1) / rows_per_block, kPairThreads, 0, st>>>(
+        l.packed, n, l.ranks, l.meta, b, margin(b), generation, d_lo, d_hi);
+    if (cudaGetLastError() != cudaSuccess) return GA_ECUDA;
+    int device_status = GA_OK;
+    if (cudaMemcpyAsync(&device_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return GA_ECUDA;
+    return device_status;
+}

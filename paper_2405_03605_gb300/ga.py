@@ -22,7 +22,7 @@ EXPORTED = (
     "ga_create", "ga_migrate_policy", "ga_step", "ga_sync", "ga_generation",
     "ga_launch_count", "ga_population", "ga_snapshot", "ga_snapshot_device", "ga_load",
     "ga_mrca_bounds", "ga_mrca_bounds_device", "ga_destroy", "ga_strerror", "ga_reset",
-    "ga_curation_sites",
+    "ga_curation_sites", "ga_mrca_bounds_noalloc",
 )
 
 
@@ -274,3 +274,20 @@ def curation_sites(policy, surface_sites, t0, count, stream=None):
     _check(load_library().ga_curation_sites(policy, surface_sites, t0, count, out.data_ptr(),
                                             st or None), "ga_curation_sites")
     return out
+
+
+def mrca_bounds_noalloc(records_ptr, record_bytes, n_agents, curation, surface_sites,
+                        differentia_bits, generation, ids, lo, hi, stream=None):
+    """ga_mrca_bounds_noalloc: MRCA bounds for callers that cannot allocate device memory.
+    records_ptr: device address of the canonical records; ids, lo, hi: device tensors with
+    32-bit elements, caller-allocated.  Synchronous; raises GaError on failure."""
+    import torch
+    lib = load_library()
+    f = lib.ga_mrca_bounds_noalloc
+    f.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                  C.c_uint32, C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(f(records_ptr, record_bytes, n_agents, curation, surface_sites, differentia_bits,
+             generation, ids.data_ptr(), ids.numel(), lo.data_ptr(), hi.data_ptr(), st or None),
+           "ga_mrca_bounds_noalloc")

@@ -22,6 +22,26 @@ struct Key {
     uint32_t k0, k1;
 };
 
+// The ten round keys (key + r * Weyl increment, mod 2^32) depend only on the seed; the
+// island step receives them precomputed as kernel parameters, so each round XORs its key
+// straight from the constant bank instead of keeping a schedule in registers.
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+inline RoundKeys round_keys(Key key)
+{
+    RoundKeys rk;
+    uint32_t k0 = key.k0, k1 = key.k1;
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = k0;
+        rk.k1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return rk;
+}
+
 __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                         Key key)
 {
@@ -38,6 +58,23 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
         c2 = n2;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           const RoundKeys &rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t a = static_cast<uint64_t>(c0) * 0xD2511F53ull;
+        const uint64_t b = static_cast<uint64_t>(c2) * 0xCD9E8D57ull;
+        const uint32_t n0 = static_cast<uint32_t>(b >> 32) ^ c1 ^ rk.k0[r];
+        const uint32_t n2 = static_cast<uint32_t>(a >> 32) ^ c3 ^ rk.k1[r];
+        c1 = static_cast<uint32_t>(b);
+        c3 = static_cast<uint32_t>(a);
+        c0 = n0;
+        c2 = n2;
     }
     return make_uint4(c0, c1, c2, c3);
 }

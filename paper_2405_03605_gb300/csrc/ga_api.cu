@@ -168,6 +168,8 @@ int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_
     }
     uint8_t *base = static_cast<uint8_t *>(run->workspace);
     run->d_status = reinterpret_cast<int *>(base);
+    run->d_sites = reinterpret_cast<int32_t *>(base + ga::kStatusBytes);
+    run->sites_base = 0;
     run->pop[0] = base + ga::kHeaderBytes;
     run->pop[1] = base + ga::kHeaderBytes + buffer_stride(cfg);
     run->cur = 0;
@@ -203,23 +205,31 @@ int ga_step(ga_run *run, uint32_t n_gens)
     if (!run) return GA_EINVAL;
     if (run->generation + n_gens > 0xFFFFFFFFull) return GA_EINVAL;
     while (n_gens > 0) {
-        const uint64_t g = run->generation;
-        uint64_t len = n_gens;
-        bool migrate = false;
-        if (run->per_neighbor) {
-            migrate = (g % run->every_k) == 0;
-            const uint64_t next = (g / run->every_k + 1) * run->every_k;
-            if (next - g < len) len = next - g;
-        }
-        if (len > ga::kMaxGensPerLaunch) len = ga::kMaxGensPerLaunch;
-        const int rc = cuda_rc(ga::launch_island_step(run, run->pop[run->cur],
-                                                      run->pop[run->cur ^ 1],
-                                                      static_cast<uint32_t>(g),
-                                                      static_cast<uint32_t>(len), migrate));
+        // curation sites of the next chunk of generations, computed on the device once
+        const uint32_t chunk = n_gens < ga::kSiteTableCap ? n_gens : ga::kSiteTableCap;
+        int rc = cuda_rc(ga::launch_site_table(run, static_cast<uint32_t>(run->generation), chunk));
         if (rc != GA_OK) return rc;
-        run->cur ^= 1;
-        run->generation += len;
-        n_gens -= static_cast<uint32_t>(len);
+        run->sites_base = run->generation;
+        uint32_t left = chunk;
+        while (left > 0) {
+            const uint64_t g = run->generation;
+            uint64_t len = left;
+            bool migrate = false;
+            if (run->per_neighbor) {
+                migrate = (g % run->every_k) == 0;
+                const uint64_t next = (g / run->every_k + 1) * run->every_k;
+                if (next - g < len) len = next - g;
+            }
+            if (len > ga::kMaxGensPerLaunch) len = ga::kMaxGensPerLaunch;
+            rc = cuda_rc(ga::launch_island_step(run, run->pop[run->cur], run->pop[run->cur ^ 1],
+                                                static_cast<uint32_t>(g),
+                                                static_cast<uint32_t>(len), migrate));
+            if (rc != GA_OK) return rc;
+            run->cur ^= 1;
+            run->generation += len;
+            left -= static_cast<uint32_t>(len);
+        }
+        n_gens -= chunk;
     }
     return GA_OK;
 }

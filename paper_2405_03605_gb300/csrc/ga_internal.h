@@ -25,13 +25,19 @@ struct ga_run {
     size_t workspace_bytes;
     bool owns_workspace;
     int *d_status;       // device error word (GA_OK or a GA_E* code), in the workspace header
+    int32_t *d_sites;    // curation site of generation sites_base + i (workspace header)
+    uint64_t sites_base;
     uint8_t *pop[2];     // double-buffered population
     int cur;             // index of the current population buffer
 };
 
 namespace ga {
 
-constexpr size_t kHeaderBytes = 256;
+// Workspace header: the device status word (first 256 bytes), then the curation-site table
+// of the generations a ga_step call is about to run (one int32 per generation).
+constexpr size_t kStatusBytes = 256;
+constexpr uint32_t kSiteTableCap = 4096;
+constexpr size_t kHeaderBytes = kStatusBytes + kSiteTableCap * sizeof(int32_t);
 
 // Largest number of generations one island-step launch runs without migration.
 constexpr uint32_t kMaxGensPerLaunch = 256;
@@ -42,6 +48,8 @@ bool step_supported(uint32_t island_size, uint32_t surface_words);
 cudaError_t launch_founder(ga_run *run, void *dst);
 cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t g0,
                                uint32_t n_gens, bool migrate);
+// Fill the site table with the curation sites of generations [g0, g0 + count).
+cudaError_t launch_site_table(ga_run *run, uint32_t g0, uint32_t count);
 cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t *d_lo,
                         uint32_t *d_hi, void *scratch);
 size_t mrca_scratch_bytes(const ga_run *run, uint32_t n);

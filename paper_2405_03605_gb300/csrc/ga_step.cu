@@ -39,6 +39,7 @@ struct StepArgs {
     RoundKeys rk;
     uint32_t run_id;
     uint32_t g0, n_gens, migrate;
+    const int32_t *__restrict__ gen_sites;  // curation site of generation g0 + i
 };
 
 // Candidate trait of slot `sel` of this lane's island.  For N <= 32 `sel` may carry extra
@@ -79,10 +80,20 @@ __device__ __forceinline__ void birth_draws(uint4 (&w)[Shape<N>::A], const StepA
 }
 
 // Evaluation, tournament, copy, mutation and hstrat deposit of one generation, in place.
-template <int N, int SW>
+// Closed-form curation site, called only for agents whose counter differs from the
+// generation (never in synchronous runs); kept out of line so the common path stays a load.
+__device__ __noinline__ int curation_site_of(uint32_t policy, uint32_t log2_sites, uint32_t sites,
+                                            uint32_t T)
+{
+    return curation_site(policy, log2_sites, sites, T);
+}
+
+// g: the generation; gen_site: its curation site, valid for agents whose counter is g (all
+// agents in synchronous runs) -- any other counter takes the closed form.
+template <int N, int SW, int TS>
 __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
                                           const uint4 (&w)[Shape<N>::A], const StepArgs &p,
-                                          unsigned mask)
+                                          unsigned mask, uint32_t g, int gen_site)
 {
     constexpr int A = Shape<N>::A, SEG = Shape<N>::SEG, LOGN = Shape<N>::LOGN;
     constexpr int LW = 2 + SW;
@@ -98,7 +109,11 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
         int best_trait = 0;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            if (static_cast<uint32_t>(i) >= p.tsize) break;
+            if constexpr (TS > 0) {
+                if (i >= TS) break;
+            } else {
+                if (static_cast<uint32_t>(i) >= p.tsize) break;
+            }
             const uint32_t word = i < 4 ? w[ag].x : w[ag].y;
             uint32_t sel = word >> (8 * (i & 3) + 8 - LOGN);
             if constexpr (N > 32) sel &= N - 1u;
@@ -141,7 +156,8 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
         child[ag][0] = t;
 
         const uint32_t c = child[ag][1];
-        const int site = curation_site(p.policy, p.log2_sites, p.sites, c);
+        int site = gen_site;
+        if (c != g) site = curation_site_of(p.policy, p.log2_sites, p.sites, c);
         if (site >= 0) {
             const uint32_t pos = static_cast<uint32_t>(site) * p.bits;
             const uint32_t wi = pos >> 5, sh = pos & 31u;
@@ -157,8 +173,9 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
     }
 }
 
-// N: island size; SW: surface words carried per record (the record is RW words).
-template <int N, int SW>
+// N: island size; SW: surface words carried per record (the record is RW words); TS: the
+// tournament size when fixed at compile time (0: read from the arguments).
+template <int N, int SW, int TS>
 __global__ void __launch_bounds__(kStepThreads) island_step_kernel(const StepArgs p)
 {
     constexpr int A = Shape<N>::A, P = Shape<N>::P, SEG = Shape<N>::SEG;
@@ -179,8 +196,31 @@ __global__ void __launch_bounds__(kStepThreads) island_step_kernel(const StepArg
     const bool valid = island < p.n_islands;
     const unsigned mask = __ballot_sync(0xffffffffu, valid);
 
-    // this lane's records and its birth draws of generation g0: both overlap the migration
-    // bookkeeping and the block barrier below
+    // Migration bookkeeping, part 1 (threads < ML, whole warps): the immigrant loads are
+    // issued first, so their latency overlaps everything up to the block barrier.
+    const bool mig_lane = p.migrate && threadIdx.x < ML;
+    const uint32_t md = threadIdx.x & 3u;  // direction of this bookkeeping lane
+    uint32_t r = md;                       // its landing draw
+    uint4 imm[Q];
+    if (mig_lane) {
+        const uint32_t isl = island0 + (threadIdx.x >> 2);
+        if (isl < p.n_islands) {
+            // birth draw of slot d: bits 8..15 pick the immigrant, bits 16..31 its landing
+            const uint32_t u = philox_rk(p.g0, isl, md | (kBirth << 16), p.run_id, p.rk).w;
+            r = md + (((u >> 16) * static_cast<uint32_t>(N - md)) >> 16);
+            const uint32_t e = (((u >> 8) & 0xFFu) * N) >> 8;
+            const uint32_t y = isl / p.cols, x = isl - y * p.cols;
+            const uint32_t yn = md == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
+                              : md == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
+            const uint32_t xn = md == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
+                              : md == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
+            const uint4 *srec = p.src + (static_cast<size_t>(yn * p.cols + xn) * N + e) * Q;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) imm[q] = __ldg(&srec[q]);
+        }
+    }
+
+    // this lane's records and its birth draws of generation g0
     uint32_t rec[A][LW];
     uint4 w[A];
     if (valid) {
@@ -199,27 +239,11 @@ __global__ void __launch_bounds__(kStepThreads) island_step_kernel(const StepArg
         birth_draws<N>(w, p, p.g0, island, seg_lane);
     }
 
+    // Migration bookkeeping, part 2: the partial Fisher-Yates landing slots (over [0, N) in
+    // direction order, among the island's four lanes: entry e records "position r[e] now
+    // holds value v[e]", later entries winning), then records and slots to shared memory.
     if (p.migrate) {
-        if (threadIdx.x < ML) {  // whole warps: ML is a multiple of 32
-            const uint32_t li = threadIdx.x >> 2, d = threadIdx.x & 3u;
-            const uint32_t isl = island0 + li;
-            uint32_t r = d;
-            if (isl < p.n_islands) {
-                // birth draw of slot d: bits 8..15 pick the immigrant, bits 16..31 its landing
-                const uint32_t u = philox_rk(p.g0, isl, d | (kBirth << 16), p.run_id, p.rk).w;
-                r = d + (((u >> 16) * static_cast<uint32_t>(N - d)) >> 16);
-                const uint32_t e = (((u >> 8) & 0xFFu) * N) >> 8;
-                const uint32_t y = isl / p.cols, x = isl - y * p.cols;
-                const uint32_t yn = d == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
-                                  : d == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
-                const uint32_t xn = d == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
-                                  : d == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
-                const uint4 *srec = p.src + (static_cast<size_t>(yn * p.cols + xn) * N + e) * Q;
-#pragma unroll
-                for (int q = 0; q < Q; ++q) s_imm[threadIdx.x][q] = __ldg(&srec[q]);
-            }
-            // partial Fisher-Yates over [0, N) in direction order, among the island's four
-            // lanes: entry e records "position r[e] now holds value v[e]" (later wins)
+        if (mig_lane) {
             uint32_t rr[4];
 #pragma unroll
             for (int dd = 0; dd < 4; ++dd) rr[dd] = __shfl_sync(0xffffffffu, r, dd, 4);
@@ -232,10 +256,14 @@ __global__ void __launch_bounds__(kStepThreads) island_step_kernel(const StepArg
                     if (rr[e] == static_cast<uint32_t>(dd)) vd = v[e];
                     if (rr[e] == rr[dd]) vr = v[e];
                 }
-                if (static_cast<uint32_t>(dd) == d) slot = vr;
+                if (static_cast<uint32_t>(dd) == md) slot = vr;
                 v[dd] = vd;
             }
             s_slot[threadIdx.x] = slot;
+            if (island0 + (threadIdx.x >> 2) < p.n_islands) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) s_imm[threadIdx.x][q] = imm[q];
+            }
         }
         __syncthreads();
     }
@@ -261,12 +289,12 @@ __global__ void __launch_bounds__(kStepThreads) island_step_kernel(const StepArg
             }
         }
     }
-    reproduce<N, SW>(rec, w, p, mask);
+    reproduce<N, SW, TS>(rec, w, p, mask, p.g0, __ldg(&p.gen_sites[0]));
 
     // generations g0 + 1 .. g0 + n - 1: no migration, the island stays in registers
     for (uint32_t it = 1; it < p.n_gens; ++it) {
         birth_draws<N>(w, p, p.g0 + it, island, seg_lane);
-        reproduce<N, SW>(rec, w, p, mask);
+        reproduce<N, SW, TS>(rec, w, p, mask, p.g0 + it, __ldg(&p.gen_sites[it]));
     }
 
 #pragma unroll
@@ -321,24 +349,32 @@ using StepKernel = void (*)(StepArgs);
 
 // The template's surface-word count fills the record: 16-byte records carry 2 surface words,
 // 32-byte records 6 and 48-byte records 8 (words past the run's own S*b bits are zero).
-template <int N>
-StepKernel pick_sw(uint32_t surface_words)
+// Tournament size 5 (the paper's, Sec. 3) has its own instantiation; other sizes use the
+// kernel that reads the size from its arguments.
+template <int N, int SW>
+StepKernel pick_ts(uint32_t tsize)
 {
-    if (surface_words <= 2) return island_step_kernel<N, 2>;
-    if (surface_words <= 6) return island_step_kernel<N, 6>;
-    if (surface_words <= 8) return island_step_kernel<N, 8>;
+    return tsize == 5 ? island_step_kernel<N, SW, 5> : island_step_kernel<N, SW, 0>;
+}
+
+template <int N>
+StepKernel pick_sw(uint32_t surface_words, uint32_t tsize)
+{
+    if (surface_words <= 2) return pick_ts<N, 2>(tsize);
+    if (surface_words <= 6) return pick_ts<N, 6>(tsize);
+    if (surface_words <= 8) return pick_ts<N, 8>(tsize);
     return nullptr;
 }
 
-StepKernel pick_kernel(uint32_t island_size, uint32_t surface_words)
+StepKernel pick_kernel(uint32_t island_size, uint32_t surface_words, uint32_t tsize)
 {
     switch (island_size) {
-    case 4: return pick_sw<4>(surface_words);
-    case 8: return pick_sw<8>(surface_words);
-    case 16: return pick_sw<16>(surface_words);
-    case 32: return pick_sw<32>(surface_words);
-    case 64: return pick_sw<64>(surface_words);
-    case 128: return pick_sw<128>(surface_words);
+    case 4: return pick_sw<4>(surface_words, tsize);
+    case 8: return pick_sw<8>(surface_words, tsize);
+    case 16: return pick_sw<16>(surface_words, tsize);
+    case 32: return pick_sw<32>(surface_words, tsize);
+    case 64: return pick_sw<64>(surface_words, tsize);
+    case 128: return pick_sw<128>(surface_words, tsize);
     default: return nullptr;
     }
 }
@@ -359,7 +395,7 @@ uint32_t sm_count()
 
 bool step_supported(uint32_t island_size, uint32_t surface_words)
 {
-    return pick_kernel(island_size, surface_words) != nullptr;
+    return pick_kernel(island_size, surface_words, 1) != nullptr;
 }
 
 cudaError_t launch_founder(ga_run *run, void *dst)
@@ -381,7 +417,8 @@ cudaError_t launch_founder(ga_run *run, void *dst)
 cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t g0,
                                uint32_t n_gens, bool migrate)
 {
-    const StepKernel k = pick_kernel(run->cfg.island_size, run->surface_words);
+    const StepKernel k =
+        pick_kernel(run->cfg.island_size, run->surface_words, run->cfg.tournament_size);
     if (!k) return cudaErrorInvalidValue;
     StepArgs a;
     a.src = static_cast<const uint4 *>(src);
@@ -402,12 +439,21 @@ cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t
     a.g0 = g0;
     a.n_gens = n_gens;
     a.migrate = migrate ? 1u : 0u;
+    a.gen_sites = run->d_sites + (g0 - run->sites_base);
     const uint32_t N = run->cfg.island_size;
     const uint32_t islands_per_block = kStepWarps * (N >= 32 ? 1u : 32u / N);
     const uint32_t blocks = (run->n_islands + islands_per_block - 1) / islands_per_block;
     k<<<blocks, kStepThreads, 0, run->stream>>>(a);
     run->launches += 1;
     return cudaGetLastError();
+}
+
+cudaError_t launch_site_table(ga_run *run, uint32_t g0, uint32_t count)
+{
+    const cudaError_t e = launch_curation_sites(run->cfg.curation, run->cfg.surface_sites, g0,
+                                                count, run->d_sites, run->stream);
+    run->launches += 1;
+    return e;
 }
 
 cudaError_t launch_curation_sites(uint32_t policy, uint32_t sites, uint32_t t0, uint32_t count,

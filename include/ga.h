@@ -168,6 +168,62 @@ int ga_mrca_bounds_device(ga_run *run, const uint32_t *d_agent_ids, uint32_t n,
                           uint32_t *d_lo, uint32_t *d_hi);
 
 /*
+ * Batches: many independent runs advanced by shared launches.  The paper runs each
+ * population on its own processor (Sec. 2) and its trials one at a time (Sec. 3); a batch
+ * instead packs the islands of all member runs into one launch per class (island size,
+ * record size, seed) and generation, so small runs fill the GPU together.  Each member's
+ * results are bit-identical to stepping it alone (draws are keyed by seed, run_id,
+ * generation, island and slot).  A fixed-length chunk of generations is captured once as a
+ * CUDA graph and replayed.
+ *
+ * A run belongs to at most one batch at a time; while it does, use the batch calls to step
+ * it, and call ga_batch_sync before any per-run call that reads its state (ga_snapshot,
+ * ga_mrca_bounds, ...).  Member runs may have different shapes, mutation rates, tournament
+ * sizes, curation policies, seeds and migration policies; island sizes 8..64.
+ */
+typedef struct ga_batch ga_batch;
+
+/* Create an empty batch whose launches go to `stream` (NULL: a stream the batch creates
+   and owns).  Errors: GA_EINVAL, GA_ENOMEM, GA_ECUDA. */
+int ga_batch_create(void *stream, ga_batch **out);
+
+/* Add a run (synchronises the run's stream and the batch's stream).  GA_EINVAL if it is
+   already a member; GA_EUNSUPPORTED for island sizes without a batched kernel. */
+int ga_batch_add(ga_batch *batch, ga_run *run);
+
+/* Remove a member run (synchronises the batch's stream; the run keeps its state). */
+int ga_batch_remove(ga_batch *batch, ga_run *run);
+
+/* Number of member runs. */
+int ga_batch_size(const ga_batch *batch, uint32_t *n_runs);
+
+/* Advance every member run by n_gens generations (Sec. 2 generational cycle), on the
+   batch's stream, asynchronously.  Errors: GA_EINVAL, GA_ENOMEM, GA_ECUDA. */
+int ga_batch_step(ga_batch *batch, uint32_t n_gens);
+
+/* Wait for the batch's stream. */
+int ga_batch_sync(ga_batch *batch);
+
+/* Kernels the batch has launched (a graph replay counts its kernel nodes). */
+int ga_batch_launch_count(const ga_batch *batch, uint64_t *launches);
+
+/*
+ * Autotune the launch shape: for each class, warps per block in {4, 8, 16}; then the graph
+ * chunk length in {16, 64, 256} generations -- each candidate timed with CUDA events over
+ * trial_gens generations of the real member runs, whose state is saved before and restored
+ * after the trials (results are unchanged by any choice).  *chosen_chunk (optional) gets the
+ * chunk length.  Synchronous.  Errors: GA_EINVAL, GA_ENOMEM, GA_ECUDA.
+ */
+int ga_batch_autotune(ga_batch *batch, uint32_t trial_gens, uint32_t *chosen_chunk);
+
+/* Island size and warps per block of class `index` (classes ordered by first member). */
+int ga_batch_class_warps(const ga_batch *batch, uint32_t index, uint32_t *island_size,
+                         uint32_t *warps);
+
+/* Destroy the batch (synchronises its stream; member runs are left intact). */
+int ga_batch_destroy(ga_batch *batch);
+
+/*
  * Curation table: d_sites[i] = site that the deposit of rank t0 + i overwrites under the
  * given policy over S sites, or -1 when that rank is not stored (hstrat update of Sec. 2;
  * the policies are those of GA_STEADY / GA_TILTED / GA_HYBRID).  Computed by a kernel on

@@ -1,0 +1,556 @@
+// ga_batch.cu -- many independent runs advanced together.
+//
+// Runs of one batch share each generation's launches: one launch per class (island size,
+// record size, seed) and generation covers every member run of that class, each block
+// looking up its run and its unit within the run.  Results are bit-identical to stepping each
+// run alone: every draw is keyed by (seed; generation, island, slot, purpose, run_id), and
+// the block body is the same as the single-run kernel's.
+//
+// A chunk of generations is a fixed launch sequence -- the curation-site table of the chunk,
+// one launch per class and generation, then a tiny kernel that advances every run's
+// generation and buffer parity on the device -- so it is captured once into a CUDA graph and
+// replayed; the per-launch generation offset is a kernel parameter, the per-run state lives
+// in device descriptors.
+//
+// The autotuner times, on the real member runs (their state is saved and restored around
+// the trials), warps per block for each class and the graph's chunk length, and keeps the
+// fastest; the choice changes no result.
+#include <algorithm>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "ga_device.cuh"
+#include "ga_internal.h"
+#include "ga_island.cuh"
+
+namespace ga {
+namespace {
+
+// Per-run state on the device.  g and cur are the generation and current buffer at the start
+// of the chunk being executed; the advance kernel moves them at the end of each chunk.
+struct RunDesc {
+    const uint4 *pop[2];
+    uint32_t rows, cols, n_islands, tsize;
+    uint32_t theta_ben, theta_del, policy, log2_sites;
+    uint32_t sites, bits, run_id, per_neighbor;
+    uint32_t every_k, g, cur, pad;
+};
+
+struct BatchArgs {
+    const RunDesc *__restrict__ runs;
+    const uint32_t *__restrict__ unit_run;    // block -> run index
+    const uint32_t *__restrict__ unit_local;  // block -> unit within the run
+    const int32_t *__restrict__ sites;        // [run][chunk] curation sites of the chunk
+    uint32_t chunk, dg;                       // chunk length, generation within the chunk
+    RoundKeys rk;
+};
+
+template <int N, int SW, int W>
+__global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
+{
+    const uint32_t run = __ldg(&a.unit_run[blockIdx.x]);
+    const RunDesc &d = a.runs[run];
+    const uint32_t cur = d.cur ^ (a.dg & 1u);
+    RunParams r;
+    r.src = d.pop[cur];
+    r.dst = const_cast<uint4 *>(d.pop[cur ^ 1u]);
+    r.rows = d.rows;
+    r.cols = d.cols;
+    r.n_islands = d.n_islands;
+    r.tsize = d.tsize;
+    r.theta_ben = d.theta_ben;
+    r.theta_del = d.theta_del;
+    r.policy = d.policy;
+    r.log2_sites = d.log2_sites;
+    r.sites = d.sites;
+    r.bits = d.bits;
+    r.run_id = d.run_id;
+    r.g0 = d.g + a.dg;
+    r.n_gens = 1;
+    r.migrate = d.per_neighbor && (d.every_k == 1u || r.g0 % d.every_k == 0u);
+    r.gen_sites = a.sites + static_cast<size_t>(run) * a.chunk + a.dg;
+    step_block<N, SW, 0, W>(r, a.rk, __ldg(&a.unit_local[blockIdx.x]));
+}
+
+__global__ void batch_sites_kernel(const RunDesc *__restrict__ runs, uint32_t n_runs,
+                                   uint32_t chunk, int32_t *__restrict__ sites)
+{
+    const uint32_t total = n_runs * chunk;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += gridDim.x * blockDim.x) {
+        const RunDesc &d = runs[i / chunk];
+        sites[i] = curation_site(d.policy, d.log2_sites, d.sites, d.g + i % chunk);
+    }
+}
+
+__global__ void batch_advance_kernel(RunDesc *__restrict__ runs, uint32_t n_runs, uint32_t gens)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_runs) {
+        runs[i].g += gens;
+        runs[i].cur ^= gens & 1u;
+    }
+}
+
+using BatchKernel = void (*)(BatchArgs);
+
+template <int N, int SW>
+BatchKernel pick_w(uint32_t warps)
+{
+    switch (warps) {
+    case 4: return batch_step_kernel<N, SW, 4>;
+    case 8: return batch_step_kernel<N, SW, 8>;
+    case 16: return batch_step_kernel<N, SW, 16>;
+    default: return nullptr;
+    }
+}
+
+template <int N>
+BatchKernel pick_sw(uint32_t sw, uint32_t warps)
+{
+    if (sw <= 2) return pick_w<N, 2>(warps);
+    if (sw <= 6) return pick_w<N, 6>(warps);
+    if (sw <= 8) return pick_w<N, 8>(warps);
+    return nullptr;
+}
+
+BatchKernel pick(uint32_t n, uint32_t sw, uint32_t warps)
+{
+    switch (n) {
+    case 8: return pick_sw<8>(sw, warps);
+    case 16: return pick_sw<16>(sw, warps);
+    case 32: return pick_sw<32>(sw, warps);
+    case 64: return pick_sw<64>(sw, warps);
+    default: return nullptr;
+    }
+}
+
+constexpr uint32_t kWarpChoices[] = {4, 8, 16};
+constexpr uint32_t kChunkChoices[] = {16, 64, 256};
+
+struct Class {
+    uint32_t island_size, sw_class;
+    uint64_t seed;
+    uint32_t warps = 8;
+    std::vector<uint32_t> members;  // indices into the batch's run list
+    uint32_t *d_unit_run = nullptr, *d_unit_local = nullptr;
+    uint32_t units = 0;
+};
+
+uint32_t sw_class(uint32_t surface_words) { return surface_words <= 2 ? 2 : surface_words <= 6 ? 6 : 8; }
+
+}  // namespace
+}  // namespace ga
+
+struct ga_batch {
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    std::vector<ga_run *> runs;
+    std::vector<ga::Class> classes;
+    ga::RunDesc *d_runs = nullptr;
+    int32_t *d_sites = nullptr;
+    uint32_t sites_cap = 0;  // chunk length the site table holds
+    uint32_t chunk = 64;
+    bool dirty = true;
+    cudaGraphExec_t graph = nullptr;
+    uint32_t graph_chunk = 0;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+int rc_of(cudaError_t e) { return e == cudaSuccess ? GA_OK : GA_ECUDA; }
+
+void free_device(ga_batch *b)
+{
+    for (auto &c : b->classes) {
+        cudaFree(c.d_unit_run);
+        cudaFree(c.d_unit_local);
+        c.d_unit_run = c.d_unit_local = nullptr;
+    }
+    cudaFree(b->d_runs);
+    cudaFree(b->d_sites);
+    b->d_runs = nullptr;
+    b->d_sites = nullptr;
+    b->sites_cap = 0;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_chunk = 0;
+}
+
+// (Re)build classes, descriptors and block tables after membership or tuning changes.
+int rebuild(ga_batch *b)
+{
+    std::map<std::tuple<uint32_t, uint32_t, uint64_t>, uint32_t> warps_of;
+    for (const auto &c : b->classes) warps_of[{c.island_size, c.sw_class, c.seed}] = c.warps;
+    free_device(b);
+    b->classes.clear();
+    std::map<std::tuple<uint32_t, uint32_t, uint64_t>, size_t> index;
+    for (uint32_t i = 0; i < b->runs.size(); ++i) {
+        const ga_run *r = b->runs[i];
+        const auto key = std::make_tuple(r->cfg.island_size, ga::sw_class(r->surface_words), r->cfg.seed);
+        auto it = index.find(key);
+        if (it == index.end()) {
+            ga::Class c;
+            c.island_size = std::get<0>(key);
+            c.sw_class = std::get<1>(key);
+            c.seed = std::get<2>(key);
+            auto w = warps_of.find(key);
+            if (w != warps_of.end()) c.warps = w->second;
+            index[key] = b->classes.size();
+            b->classes.push_back(c);
+            it = index.find(key);
+        }
+        b->classes[it->second].members.push_back(i);
+    }
+    const size_t n = b->runs.size();
+    if (n == 0) {
+        b->dirty = false;
+        return GA_OK;
+    }
+    std::vector<ga::RunDesc> desc(n);
+    for (size_t i = 0; i < n; ++i) {
+        const ga_run *r = b->runs[i];
+        ga::RunDesc &d = desc[i];
+        d.pop[0] = reinterpret_cast<const uint4 *>(r->pop[0]);
+        d.pop[1] = reinterpret_cast<const uint4 *>(r->pop[1]);
+        d.rows = r->cfg.rows;
+        d.cols = r->cfg.cols;
+        d.n_islands = r->n_islands;
+        d.tsize = r->cfg.tournament_size;
+        d.theta_ben = r->theta_ben;
+        d.theta_del = r->theta_del;
+        d.policy = r->cfg.curation;
+        d.log2_sites = r->log2_sites;
+        d.sites = r->cfg.surface_sites;
+        d.bits = r->cfg.differentia_bits;
+        d.run_id = r->cfg.run_id;
+        d.per_neighbor = r->per_neighbor;
+        d.every_k = r->every_k;
+        d.g = static_cast<uint32_t>(r->generation);
+        d.cur = static_cast<uint32_t>(r->cur);
+        d.pad = 0;
+    }
+    if (cudaMalloc(&b->d_runs, n * sizeof(ga::RunDesc)) != cudaSuccess) return GA_ENOMEM;
+    int rc = rc_of(cudaMemcpyAsync(b->d_runs, desc.data(), n * sizeof(ga::RunDesc),
+                                   cudaMemcpyHostToDevice, b->stream));
+    if (rc != GA_OK) return rc;
+    for (auto &c : b->classes) {
+        const uint32_t per_warp = c.island_size >= 32 ? 1u : 32u / c.island_size;
+        const uint32_t per_block = c.warps * per_warp;
+        std::vector<uint32_t> ur, ul;
+        for (uint32_t m : c.members) {
+            const uint32_t units = (b->runs[m]->n_islands + per_block - 1) / per_block;
+            for (uint32_t u = 0; u < units; ++u) {
+                ur.push_back(m);
+                ul.push_back(u);
+            }
+        }
+        c.units = static_cast<uint32_t>(ur.size());
+        if (cudaMalloc(&c.d_unit_run, ur.size() * 4) != cudaSuccess ||
+            cudaMalloc(&c.d_unit_local, ul.size() * 4) != cudaSuccess)
+            return GA_ENOMEM;
+        rc = rc_of(cudaMemcpyAsync(c.d_unit_run, ur.data(), ur.size() * 4, cudaMemcpyHostToDevice,
+                                   b->stream));
+        if (rc == GA_OK)
+            rc = rc_of(cudaMemcpyAsync(c.d_unit_local, ul.data(), ul.size() * 4,
+                                       cudaMemcpyHostToDevice, b->stream));
+        if (rc != GA_OK) return rc;
+    }
+    rc = rc_of(cudaStreamSynchronize(b->stream));  // host vectors above go out of scope
+    if (rc != GA_OK) return rc;
+    b->dirty = false;
+    return GA_OK;
+}
+
+int ensure_sites(ga_batch *b, uint32_t chunk)
+{
+    if (b->sites_cap >= chunk) return GA_OK;
+    cudaFree(b->d_sites);
+    b->d_sites = nullptr;
+    const size_t bytes = b->runs.size() * static_cast<size_t>(chunk) * sizeof(int32_t);
+    if (cudaMalloc(&b->d_sites, bytes) != cudaSuccess) return GA_ENOMEM;
+    b->sites_cap = chunk;
+    return GA_OK;
+}
+
+// Enqueue one chunk of `gens` generations for every member run (no host synchronisation).
+int enqueue_chunk(ga_batch *b, uint32_t gens)
+{
+    const uint32_t n = static_cast<uint32_t>(b->runs.size());
+    ga::batch_sites_kernel<<<std::min<uint32_t>((n * gens + 255) / 256, 4096), 256, 0, b->stream>>>(
+        b->d_runs, n, gens, b->d_sites);
+    b->launches += 1;
+    for (uint32_t dg = 0; dg < gens; ++dg) {
+        for (const auto &c : b->classes) {
+            const ga::BatchKernel k = ga::pick(c.island_size, c.sw_class, c.warps);
+            if (!k) return GA_EUNSUPPORTED;
+            ga::BatchArgs a;
+            a.runs = b->d_runs;
+            a.unit_run = c.d_unit_run;
+            a.unit_local = c.d_unit_local;
+            a.sites = b->d_sites;
+            a.chunk = gens;
+            a.dg = dg;
+            a.rk = ga::round_keys(ga::Key{static_cast<uint32_t>(c.seed), static_cast<uint32_t>(c.seed >> 32)});
+            k<<<c.units, c.warps * 32, 0, b->stream>>>(a);
+            b->launches += 1;
+        }
+    }
+    ga::batch_advance_kernel<<<(n + 255) / 256, 256, 0, b->stream>>>(b->d_runs, n, gens);
+    b->launches += 1;
+    return rc_of(cudaGetLastError());
+}
+
+int capture_graph(ga_batch *b, uint32_t chunk)
+{
+    if (b->graph && b->graph_chunk == chunk) return GA_OK;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return GA_ECUDA;
+    const uint64_t before = b->launches;
+    const int rc = enqueue_chunk(b, chunk);
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    b->launches = before;  // captured, not launched
+    if (rc != GA_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc != GA_OK ? rc : GA_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        b->graph = nullptr;
+        return GA_ECUDA;
+    }
+    b->graph_chunk = chunk;
+    return GA_OK;
+}
+
+uint64_t chunk_launches(const ga_batch *b, uint32_t chunk)
+{
+    return 2 + static_cast<uint64_t>(chunk) * b->classes.size();
+}
+
+int step_device(ga_batch *b, uint32_t n_gens)
+{
+    int rc = GA_OK;
+    uint32_t left = n_gens;
+    if (left >= b->chunk) {
+        rc = ensure_sites(b, b->chunk);
+        if (rc == GA_OK) rc = capture_graph(b, b->chunk);
+        while (rc == GA_OK && left >= b->chunk) {
+            rc = rc_of(cudaGraphLaunch(b->graph, b->stream));
+            b->launches += chunk_launches(b, b->chunk);
+            left -= b->chunk;
+        }
+    }
+    if (rc == GA_OK && left > 0) {
+        rc = ensure_sites(b, left);
+        if (rc == GA_OK) rc = enqueue_chunk(b, left);
+    }
+    return rc;
+}
+
+void advance_host(ga_batch *b, uint32_t n_gens)
+{
+    for (ga_run *r : b->runs) {
+        r->generation += n_gens;
+        r->cur ^= static_cast<int>(n_gens & 1u);
+        r->launches += n_gens;  // one island-step launch per generation covers each run
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ga_batch_create(void *stream, ga_batch **out)
+{
+    if (!out) return GA_EINVAL;
+    *out = nullptr;
+    ga_batch *b = new (std::nothrow) ga_batch();
+    if (!b) return GA_ENOMEM;
+    if (stream) {
+        b->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return GA_ECUDA;
+        }
+        b->owns_stream = true;
+    }
+    *out = b;
+    return GA_OK;
+}
+
+int ga_batch_add(ga_batch *b, ga_run *run)
+{
+    if (!b || !run) return GA_EINVAL;
+    if (std::find(b->runs.begin(), b->runs.end(), run) != b->runs.end()) return GA_EINVAL;
+    if (!ga::pick(run->cfg.island_size, ga::sw_class(run->surface_words), 8)) return GA_EUNSUPPORTED;
+    if (run->generation + 1 > 0xFFFFFFFFull) return GA_EINVAL;
+    // the run's own queued work must be done before the batch stream touches its buffers
+    if (cudaStreamSynchronize(run->stream) != cudaSuccess) return GA_ECUDA;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return GA_ECUDA;
+    b->runs.push_back(run);
+    b->dirty = true;
+    return GA_OK;
+}
+
+int ga_batch_remove(ga_batch *b, ga_run *run)
+{
+    if (!b || !run) return GA_EINVAL;
+    auto it = std::find(b->runs.begin(), b->runs.end(), run);
+    if (it == b->runs.end()) return GA_EINVAL;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return GA_ECUDA;
+    b->runs.erase(it);
+    b->dirty = true;
+    return GA_OK;
+}
+
+int ga_batch_size(const ga_batch *b, uint32_t *n_runs)
+{
+    if (!b || !n_runs) return GA_EINVAL;
+    *n_runs = static_cast<uint32_t>(b->runs.size());
+    return GA_OK;
+}
+
+int ga_batch_step(ga_batch *b, uint32_t n_gens)
+{
+    if (!b) return GA_EINVAL;
+    if (b->runs.empty() || n_gens == 0) return GA_OK;
+    for (const ga_run *r : b->runs)
+        if (r->generation + n_gens > 0xFFFFFFFFull) return GA_EINVAL;
+    if (b->dirty) {
+        const int rc = rebuild(b);
+        if (rc != GA_OK) return rc;
+    }
+    const int rc = step_device(b, n_gens);
+    if (rc != GA_OK) return rc;
+    advance_host(b, n_gens);
+    return GA_OK;
+}
+
+int ga_batch_sync(ga_batch *b)
+{
+    if (!b) return GA_EINVAL;
+    return rc_of(cudaStreamSynchronize(b->stream));
+}
+
+int ga_batch_launch_count(const ga_batch *b, uint64_t *launches)
+{
+    if (!b || !launches) return GA_EINVAL;
+    *launches = b->launches;
+    return GA_OK;
+}
+
+int ga_batch_autotune(ga_batch *b, uint32_t trial_gens, uint32_t *chosen_chunk)
+{
+    if (!b || trial_gens == 0) return GA_EINVAL;
+    if (b->runs.empty()) return GA_OK;
+    if (b->dirty) {
+        const int rc = rebuild(b);
+        if (rc != GA_OK) return rc;
+    }
+    // save every run's current buffer so the trials leave no trace
+    std::vector<void *> saved(b->runs.size(), nullptr);
+    int rc = GA_OK;
+    for (size_t i = 0; i < b->runs.size() && rc == GA_OK; ++i) {
+        ga_run *r = b->runs[i];
+        const size_t bytes = static_cast<size_t>(r->n_agents) * r->record_bytes;
+        if (cudaMalloc(&saved[i], bytes) != cudaSuccess) rc = GA_ENOMEM;
+        else rc = rc_of(cudaMemcpyAsync(saved[i], r->pop[r->cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == GA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = GA_ECUDA;
+    auto restore = [&]() {
+        for (size_t i = 0; i < b->runs.size(); ++i) {
+            ga_run *r = b->runs[i];
+            if (saved[i])
+                cudaMemcpyAsync(r->pop[r->cur], saved[i], static_cast<size_t>(r->n_agents) * r->record_bytes,
+                                cudaMemcpyDeviceToDevice, b->stream);
+        }
+        b->dirty = true;  // descriptors back to the runs' (unchanged) host state
+    };
+    auto timed = [&](uint32_t gens, float *ms) -> int {
+        int r2 = rebuild(b);
+        if (r2 != GA_OK) return r2;
+        r2 = step_device(b, gens);  // warm (graph capture, caches)
+        if (r2 != GA_OK) return r2;
+        if (cudaEventRecord(e0, b->stream) != cudaSuccess) return GA_ECUDA;
+        r2 = step_device(b, gens);
+        if (r2 != GA_OK) return r2;
+        if (cudaEventRecord(e1, b->stream) != cudaSuccess) return GA_ECUDA;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return GA_ECUDA;
+        return rc_of(cudaEventElapsedTime(ms, e0, e1));
+    };
+    const uint32_t saved_chunk = b->chunk;
+    // warps per block, class by class (the others held at their current choice)
+    b->chunk = trial_gens;
+    for (size_t ci = 0; ci < b->classes.size() && rc == GA_OK; ++ci) {
+        float best = 3.4e38f;
+        uint32_t best_w = b->classes[ci].warps;
+        for (uint32_t w : ga::kWarpChoices) {
+            b->classes[ci].warps = w;
+            float ms = 0.f;
+            rc = timed(trial_gens, &ms);
+            restore();
+            if (rc != GA_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_w = w;
+            }
+        }
+        b->classes[ci].warps = best_w;
+    }
+    // graph chunk length
+    uint32_t best_chunk = saved_chunk;
+    if (rc == GA_OK) {
+        float best = 3.4e38f;
+        for (uint32_t c : ga::kChunkChoices) {
+            b->chunk = c;
+            float ms = 0.f;
+            rc = timed(c, &ms);
+            restore();
+            if (rc != GA_OK) break;
+            if (ms / c < best) {
+                best = ms / c;
+                best_chunk = c;
+            }
+        }
+    }
+    b->chunk = best_chunk;
+    if (chosen_chunk) *chosen_chunk = best_chunk;
+    cudaStreamSynchronize(b->stream);
+    for (void *p : saved) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    b->dirty = true;
+    return rc;
+}
+
+int ga_batch_class_warps(const ga_batch *b, uint32_t index, uint32_t *island_size,
+                         uint32_t *warps)
+{
+    if (!b || !island_size || !warps || index >= b->classes.size()) return GA_EINVAL;
+    *island_size = b->classes[index].island_size;
+    *warps = b->classes[index].warps;
+    return GA_OK;
+}
+
+int ga_batch_destroy(ga_batch *b)
+{
+    if (!b) return GA_EINVAL;
+    int rc = rc_of(cudaStreamSynchronize(b->stream));
+    free_device(b);
+    if (b->owns_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return rc;
+}
+
+}  // extern "C"

@@ -22,7 +22,9 @@ EXPORTED = (
     "ga_create", "ga_migrate_policy", "ga_step", "ga_sync", "ga_generation",
     "ga_launch_count", "ga_population", "ga_snapshot", "ga_snapshot_device", "ga_load",
     "ga_mrca_bounds", "ga_mrca_bounds_device", "ga_destroy", "ga_strerror", "ga_reset",
-    "ga_curation_sites", "ga_mrca_bounds_noalloc",
+    "ga_curation_sites", "ga_mrca_bounds_noalloc", "ga_batch_create", "ga_batch_add",
+    "ga_batch_remove", "ga_batch_size", "ga_batch_step", "ga_batch_sync",
+    "ga_batch_launch_count", "ga_batch_autotune", "ga_batch_class_warps", "ga_batch_destroy",
 )
 
 
@@ -81,6 +83,16 @@ def load_library(path=LIB_PATH):
         "ga_strerror": ([C.c_int], C.c_char_p),
         "ga_reset": ([vp], C.c_int),
         "ga_curation_sites": ([u32, u32, u32, u32, vp, vp], C.c_int),
+        "ga_batch_create": ([vp, C.POINTER(vp)], C.c_int),
+        "ga_batch_add": ([vp, vp], C.c_int),
+        "ga_batch_remove": ([vp, vp], C.c_int),
+        "ga_batch_size": ([vp, C.POINTER(u32)], C.c_int),
+        "ga_batch_step": ([vp, u32], C.c_int),
+        "ga_batch_sync": ([vp], C.c_int),
+        "ga_batch_launch_count": ([vp, C.POINTER(u64)], C.c_int),
+        "ga_batch_autotune": ([vp, u32, C.POINTER(u32)], C.c_int),
+        "ga_batch_class_warps": ([vp, u32, C.POINTER(u32), C.POINTER(u32)], C.c_int),
+        "ga_batch_destroy": ([vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -291,3 +303,65 @@ def mrca_bounds_noalloc(records_ptr, record_bytes, n_agents, curation, surface_s
     _check(f(records_ptr, record_bytes, n_agents, curation, surface_sites, differentia_bits,
              generation, ids.data_ptr(), ids.numel(), lo.data_ptr(), hi.data_ptr(), st or None),
            "ga_mrca_bounds_noalloc")
+
+
+class Batch:
+    """Several runs advanced by shared launches (``ga_batch_*``).  Member results are
+    bit-identical to stepping each run alone.  stream: a torch.cuda.Stream (default: one the
+    batch creates)."""
+
+    def __init__(self, runs=(), stream=None):
+        self.lib = load_library()
+        self.stream = stream
+        h = C.c_void_p()
+        _check(self.lib.ga_batch_create(stream.cuda_stream if stream is not None else None,
+                                        C.byref(h)), "ga_batch_create")
+        self._h = h
+        self.runs = []
+        for r in runs:
+            self.add(r)
+
+    def add(self, run):
+        _check(self.lib.ga_batch_add(self._h, run._h), "ga_batch_add")
+        self.runs.append(run)
+
+    def remove(self, run):
+        _check(self.lib.ga_batch_remove(self._h, run._h), "ga_batch_remove")
+        self.runs.remove(run)
+
+    def step(self, n_gens):
+        _check(self.lib.ga_batch_step(self._h, n_gens), "ga_batch_step")
+
+    def sync(self):
+        _check(self.lib.ga_batch_sync(self._h), "ga_batch_sync")
+
+    def autotune(self, trial_gens=16):
+        chunk = C.c_uint32()
+        _check(self.lib.ga_batch_autotune(self._h, trial_gens, C.byref(chunk)),
+               "ga_batch_autotune")
+        warps = []
+        i = 0
+        while True:
+            n, w = C.c_uint32(), C.c_uint32()
+            if self.lib.ga_batch_class_warps(self._h, i, C.byref(n), C.byref(w)) != GA_OK:
+                break
+            warps.append((n.value, w.value))
+            i += 1
+        return {"chunk": chunk.value, "class_warps": warps}
+
+    @property
+    def launches(self):
+        n = C.c_uint64()
+        _check(self.lib.ga_batch_launch_count(self._h, C.byref(n)), "ga_batch_launch_count")
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.ga_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -45,6 +45,13 @@ def parse_args():
     p.add_argument("--sample", type=int, default=4096)
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--batch-runs", type=int, default=256)
+    p.add_argument("--batch-gens", type=int, default=2000)
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=200)
+    p.add_argument("--variants", action="store_true")
+    p.add_argument("--variant-gens", type=int, default=1000)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -295,6 +302,11 @@ def run_ours(args, rank, world, local):
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(args, shs, ids_h, world)
+    batched = None
+    if not args.no_batch:
+        batched = measure_batch(args, rank)
+    served = measure_serve(args) if args.serve and rank == 0 else None
+    variants = measure_variants(args) if args.variants and rank == 0 else None
 
     for r in runs:
         r.close()
@@ -318,12 +330,144 @@ def run_ours(args, rank, world, local):
                      "bytes_per_launch": bytes_per_launch,
                      "avg_launch_us": avg_launch_s * 1e6},
         "mrca_ms_per_run": mrca_ms,
+        "batched_vs_serial": batched,
+        **({"serving": served} if served is not None else {}),
+        **({"variants": variants} if variants is not None else {}),
         "gpu_launches": launches,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
+
+
+def measure_batch(args, rank):
+    """Heterogeneous replicate runs (grid sides from {16..256}, islands of 16/32/64, p_ben and
+    p_del log-uniform on [1e-4, 1e-1], tournament size 2..8), each for the same generation
+    count: once as one autotuned batch (shared launches, CUDA-graph chunks), once as serial
+    per-run launches of the same runs on the same stream.  Both timed with CUDA events from
+    founder populations; end states compared on the device."""
+    import torch
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import batch_shapes
+
+    shapes = [s.with_(run_id=s.run_id + 100000 * rank)
+              for s in batch_shapes(args.batch_runs, seed=42, generations=args.batch_gens)]
+    gens = args.batch_gens
+    stream = torch.cuda.Stream()
+    runs = [ga.Run(s, stream=stream) for s in shapes]
+    batch = ga.Batch(runs, stream=stream)
+    tune = batch.autotune(trial_gens=8)
+    batch.step(tune["chunk"])  # capture and warm the graph
+    batch.sync()
+    for r in runs:
+        r.reset()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = batch.launches
+    e0.record(stream)
+    batch.step(gens)
+    e1.record(stream)
+    batch.sync()
+    batched_ms = e0.elapsed_time(e1)
+    batched_launches = batch.launches - l0
+
+    alone = [ga.Run(s, stream=stream) for s in shapes]
+    for r in alone:
+        r.step(2)
+        r.reset()
+    torch.cuda.synchronize()
+    l0 = sum(r.launches for r in alone)
+    e0.record(stream)
+    for r in alone:
+        r.step(gens)
+    e1.record(stream)
+    stream.synchronize()
+    serial_ms = e0.elapsed_time(e1)
+    serial_launches = sum(r.launches for r in alone) - l0
+    with torch.cuda.stream(stream):
+        identical = all(torch.equal(a.snapshot_device(), b.snapshot_device())
+                        for a, b in zip(runs, alone))
+    stream.synchronize()
+    agent_gens = float(sum(s.n_agents for s in shapes)) * gens
+    batch.close()
+    for r in runs + alone:
+        r.close()
+    return {
+        "workload": (f"{len(shapes)} runs, grid sides from {{16,32,64,128,256}}, islands of "
+                     f"16/32/64, p log-uniform [1e-4,1e-1], tournament 2..8, {gens} gens"),
+        "agents_total": int(sum(s.n_agents for s in shapes)),
+        "batched": agent_gens / (batched_ms / 1000.0),
+        "serial": agent_gens / (serial_ms / 1000.0),
+        "unit": UNIT,
+        "ratio": serial_ms / batched_ms,
+        "batched_ms": batched_ms, "serial_ms": serial_ms,
+        "batched_launches": batched_launches, "serial_launches": serial_launches,
+        "autotune": tune,
+        "identical": bool(identical),
+    }
+
+
+def measure_variants(args):
+    """4,194,304-agent surface/genome variants (256-site steady, 32-site 8-bit tilted, 64-site
+    hybrid), islands of 16/32/64, migration every 1/4/16 generations: agent-generations/s
+    from founder populations, CUDA events on the run's stream, with the algorithmic HBM
+    bytes per agent-generation (record in and out once per launch plus the immigrant
+    records, 2G/k + 4G/(N k)) turned into a fraction of the measured copy bandwidth."""
+    import torch
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import variant_shapes
+
+    peak, _ = measured_peaks()
+    gens = args.variant_gens
+    stream = torch.cuda.Stream()
+    out = []
+    for n in (16, 32, 64):
+        for k in (1, 4, 16):
+            for name, sh in variant_shapes(n, migrate_every=k, generations=gens).items():
+                r = ga.Run(sh, stream=stream)
+                r.step(2 * k)
+                r.reset()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r.step(gens)
+                e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1)
+                rate = sh.n_agents * gens / (ms / 1000.0)
+                G = r.record_bytes
+                b_alg = 2 * G / k + 4 * G / (n * k)
+                out.append({"variant": name, "island_size": n, "migrate_every": k,
+                            "record_bytes": G, "agent_gens_per_s": rate,
+                            "hbm_frac": rate * b_alg / 1e9 / peak})
+                r.close()
+    return {"agents": 4194304, "generations": gens, "runs": out}
+
+
+def measure_serve(args):
+    """Poisson stream (mean 50 requests/s) of GA runs with agents log-uniform on [1e4, 1e7]
+    and generations log-uniform on [100, 10000], served with continuous batching under an
+    HBM budget, then the same trace one run at a time.  Latency = completion - arrival."""
+    import torch
+    from paper_2405_03605_gb300 import serve
+    from paper_2405_03605_gb300.workloads import serve_trace
+
+    trace = serve_trace(n_requests=args.serve_requests, rate_hz=50.0, seed=42)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(160e9, 0.8 * free))
+    cont = serve.serve_continuous(trace, budget, chunk_gens=64, autotune=True)
+    single = serve.serve_one_at_a_time(trace)
+    out = {}
+    for name, rep in (("continuous", cont), ("one_at_a_time", single)):
+        out[name] = {"throughput": rep.throughput, "unit": UNIT,
+                     "p50_s": rep.percentile(50), "p99_s": rep.percentile(99),
+                     "makespan_s": rep.makespan, "launches": rep.launches}
+    out["requests"] = len(trace)
+    out["hbm_budget_bytes"] = budget
+    out["peak_resident_bytes"] = cont.peak_bytes
+    out["throughput_ratio"] = cont.throughput / single.throughput
+    return out
 
 
 def measure_e2e(args, shs, ids_h, world):

@@ -176,9 +176,9 @@ int ga_mrca_bounds_device(ga_run *run, const uint32_t *d_agent_ids, uint32_t n,
  * generation, island and slot).  A fixed-length chunk of generations is captured once as a
  * CUDA graph and replayed.
  *
- * A run belongs to at most one batch at a time; while it does, use the batch calls to step
- * it, and call ga_batch_sync before any per-run call that reads its state (ga_snapshot,
- * ga_mrca_bounds, ...).  Member runs may have different shapes, mutation rates, tournament
+ * A run belongs to at most one batch at a time.  Call ga_batch_sync before any per-run call
+ * on a member (ga_snapshot, ga_mrca_bounds, ga_step, ga_reset, ga_load, ...); a member whose
+ * generation or buffer changed through such calls is picked up by the next ga_batch_step.  Member runs may have different shapes, mutation rates, tournament
  * sizes, curation policies, seeds and migration policies; island sizes 8..64.
  */
 typedef struct ga_batch ga_batch;

@@ -148,6 +148,7 @@ struct ga_batch {
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
     std::vector<ga_run *> runs;
+    std::vector<std::pair<uint64_t, int>> expect;  // members' (generation, cur) the device holds
     std::vector<ga::Class> classes;
     ga::RunDesc *d_runs = nullptr;
     int32_t *d_sites = nullptr;
@@ -261,8 +262,20 @@ int rebuild(ga_batch *b)
     }
     rc = rc_of(cudaStreamSynchronize(b->stream));  // host vectors above go out of scope
     if (rc != GA_OK) return rc;
+    b->expect.clear();
+    for (const ga_run *r : b->runs) b->expect.emplace_back(r->generation, r->cur);
     b->dirty = false;
     return GA_OK;
+}
+
+// A member stepped, reset or loaded outside the batch no longer matches the descriptors.
+bool members_moved(const ga_batch *b)
+{
+    if (b->expect.size() != b->runs.size()) return true;
+    for (size_t i = 0; i < b->runs.size(); ++i)
+        if (b->expect[i].first != b->runs[i]->generation || b->expect[i].second != b->runs[i]->cur)
+            return true;
+    return false;
 }
 
 int ensure_sites(ga_batch *b, uint32_t chunk)
@@ -357,10 +370,12 @@ int step_device(ga_batch *b, uint32_t n_gens)
 
 void advance_host(ga_batch *b, uint32_t n_gens)
 {
-    for (ga_run *r : b->runs) {
+    for (size_t i = 0; i < b->runs.size(); ++i) {
+        ga_run *r = b->runs[i];
         r->generation += n_gens;
         r->cur ^= static_cast<int>(n_gens & 1u);
         r->launches += n_gens;  // one island-step launch per generation covers each run
+        b->expect[i] = {r->generation, r->cur};
     }
 }
 
@@ -425,7 +440,10 @@ int ga_batch_step(ga_batch *b, uint32_t n_gens)
     if (b->runs.empty() || n_gens == 0) return GA_OK;
     for (const ga_run *r : b->runs)
         if (r->generation + n_gens > 0xFFFFFFFFull) return GA_EINVAL;
-    if (b->dirty) {
+    if (b->dirty || members_moved(b)) {
+        // members' own streams may still hold work queued outside the batch
+        for (const ga_run *r : b->runs)
+            if (cudaStreamSynchronize(r->stream) != cudaSuccess) return GA_ECUDA;
         const int rc = rebuild(b);
         if (rc != GA_OK) return rc;
     }

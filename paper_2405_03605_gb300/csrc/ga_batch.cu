@@ -1,7 +1,7 @@
 // ga_batch.cu -- many independent runs advanced together.
 //
 // Runs of one batch share each generation's launches: one launch per class (island size,
-// record size, seed) and generation covers every member run of that class, each block
+// record size, tournament size 5 or other, seed) and generation covers every member run of that class, each block
 // looking up its run and its unit within the run.  Results are bit-identical to stepping each
 // run alone: every draw is keyed by (seed; generation, island, slot, purpose, run_id), and
 // the block body is the same as the single-run kernel's.
@@ -47,31 +47,38 @@ struct BatchArgs {
     RoundKeys rk;
 };
 
-template <int N, int SW, int W>
+template <int N, int SW, int TS, int W>
 __global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
 {
-    const uint32_t run = __ldg(&a.unit_run[blockIdx.x]);
-    const RunDesc &d = a.runs[run];
-    const uint32_t cur = d.cur ^ (a.dg & 1u);
-    RunParams r;
-    r.src = d.pop[cur];
-    r.dst = const_cast<uint4 *>(d.pop[cur ^ 1u]);
-    r.rows = d.rows;
-    r.cols = d.cols;
-    r.n_islands = d.n_islands;
-    r.tsize = d.tsize;
-    r.theta_ben = d.theta_ben;
-    r.theta_del = d.theta_del;
-    r.policy = d.policy;
-    r.log2_sites = d.log2_sites;
-    r.sites = d.sites;
-    r.bits = d.bits;
-    r.run_id = d.run_id;
-    r.g0 = d.g + a.dg;
-    r.n_gens = 1;
-    r.migrate = d.per_neighbor && (d.every_k == 1u || r.g0 % d.every_k == 0u);
-    r.gen_sites = a.sites + static_cast<size_t>(run) * a.chunk + a.dg;
-    step_block<N, SW, 0, W>(r, a.rk, __ldg(&a.unit_local[blockIdx.x]));
+    // the block's run parameters, staged once in shared memory: the block body reads them
+    // from there (uniform, broadcast) instead of holding them in registers
+    __shared__ RunParams s_r;
+    __shared__ uint32_t s_unit;
+    if (threadIdx.x == 0) {
+        const uint32_t run = __ldg(&a.unit_run[blockIdx.x]);
+        const RunDesc &d = a.runs[run];
+        const uint32_t cur = d.cur ^ (a.dg & 1u);
+        s_r.src = d.pop[cur];
+        s_r.dst = const_cast<uint4 *>(d.pop[cur ^ 1u]);
+        s_r.rows = d.rows;
+        s_r.cols = d.cols;
+        s_r.n_islands = d.n_islands;
+        s_r.tsize = d.tsize;
+        s_r.theta_ben = d.theta_ben;
+        s_r.theta_del = d.theta_del;
+        s_r.policy = d.policy;
+        s_r.log2_sites = d.log2_sites;
+        s_r.sites = d.sites;
+        s_r.bits = d.bits;
+        s_r.run_id = d.run_id;
+        s_r.g0 = d.g + a.dg;
+        s_r.n_gens = 1;
+        s_r.migrate = d.per_neighbor && (d.every_k == 1u || s_r.g0 % d.every_k == 0u);
+        s_r.gen_sites = a.sites + static_cast<size_t>(run) * a.chunk + a.dg;
+        s_unit = __ldg(&a.unit_local[blockIdx.x]);
+    }
+    __syncthreads();
+    step_block<N, SW, TS, W>(s_r, a.rk, s_unit);
 }
 
 __global__ void batch_sites_kernel(const RunDesc *__restrict__ runs, uint32_t n_runs,
@@ -96,33 +103,41 @@ __global__ void batch_advance_kernel(RunDesc *__restrict__ runs, uint32_t n_runs
 
 using BatchKernel = void (*)(BatchArgs);
 
-template <int N, int SW>
+// Tournament size 5 (the paper's, Sec. 3) has its own instantiations; other sizes use the
+// kernels that read the size from the run.
+template <int N, int SW, int TS>
 BatchKernel pick_w(uint32_t warps)
 {
     switch (warps) {
-    case 4: return batch_step_kernel<N, SW, 4>;
-    case 8: return batch_step_kernel<N, SW, 8>;
-    case 16: return batch_step_kernel<N, SW, 16>;
+    case 4: return batch_step_kernel<N, SW, TS, 4>;
+    case 8: return batch_step_kernel<N, SW, TS, 8>;
+    case 16: return batch_step_kernel<N, SW, TS, 16>;
     default: return nullptr;
     }
 }
 
-template <int N>
-BatchKernel pick_sw(uint32_t sw, uint32_t warps)
+template <int N, int SW>
+BatchKernel pick_ts(uint32_t ts, uint32_t warps)
 {
-    if (sw <= 2) return pick_w<N, 2>(warps);
-    if (sw <= 6) return pick_w<N, 6>(warps);
-    if (sw <= 8) return pick_w<N, 8>(warps);
+    return ts == 5 ? pick_w<N, SW, 5>(warps) : pick_w<N, SW, 0>(warps);
+}
+
+template <int N>
+BatchKernel pick_sw(uint32_t sw, uint32_t ts, uint32_t warps)
+{
+    if (sw <= 2) return pick_ts<N, 2>(ts, warps);
+    if (sw <= 6) return pick_ts<N, 6>(ts, warps);
+    if (sw <= 8) return pick_ts<N, 8>(ts, warps);
     return nullptr;
 }
 
-BatchKernel pick(uint32_t n, uint32_t sw, uint32_t warps)
+BatchKernel pick(uint32_t n, uint32_t sw, uint32_t ts, uint32_t warps)
 {
     switch (n) {
-    case 8: return pick_sw<8>(sw, warps);
-    case 16: return pick_sw<16>(sw, warps);
-    case 32: return pick_sw<32>(sw, warps);
-    case 64: return pick_sw<64>(sw, warps);
+    case 8: return pick_sw<8>(sw, ts, warps);
+    case 16: return pick_sw<16>(sw, ts, warps);
+    case 32: return pick_sw<32>(sw, ts, warps);
+    case 64: return pick_sw<64>(sw, ts, warps);
     default: return nullptr;
     }
 }
@@ -131,7 +146,7 @@ constexpr uint32_t kWarpChoices[] = {4, 8, 16};
 constexpr uint32_t kChunkChoices[] = {16, 64, 256};
 
 struct Class {
-    uint32_t island_size, sw_class;
+    uint32_t island_size, sw_class, ts_class;
     uint64_t seed;
     uint32_t warps = 8;
     std::vector<uint32_t> members;  // indices into the batch's run list
@@ -140,6 +155,7 @@ struct Class {
 };
 
 uint32_t sw_class(uint32_t surface_words) { return surface_words <= 2 ? 2 : surface_words <= 6 ? 6 : 8; }
+uint32_t ts_class(uint32_t tsize) { return tsize == 5 ? 5 : 0; }
 
 }  // namespace
 }  // namespace ga
@@ -184,20 +200,22 @@ void free_device(ga_batch *b)
 // (Re)build classes, descriptors and block tables after membership or tuning changes.
 int rebuild(ga_batch *b)
 {
-    std::map<std::tuple<uint32_t, uint32_t, uint64_t>, uint32_t> warps_of;
-    for (const auto &c : b->classes) warps_of[{c.island_size, c.sw_class, c.seed}] = c.warps;
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint64_t>, uint32_t> warps_of;
+    for (const auto &c : b->classes) warps_of[{c.island_size, c.sw_class, c.ts_class, c.seed}] = c.warps;
     free_device(b);
     b->classes.clear();
-    std::map<std::tuple<uint32_t, uint32_t, uint64_t>, size_t> index;
+    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint64_t>, size_t> index;
     for (uint32_t i = 0; i < b->runs.size(); ++i) {
         const ga_run *r = b->runs[i];
-        const auto key = std::make_tuple(r->cfg.island_size, ga::sw_class(r->surface_words), r->cfg.seed);
+        const auto key = std::make_tuple(r->cfg.island_size, ga::sw_class(r->surface_words),
+                                         ga::ts_class(r->cfg.tournament_size), r->cfg.seed);
         auto it = index.find(key);
         if (it == index.end()) {
             ga::Class c;
             c.island_size = std::get<0>(key);
             c.sw_class = std::get<1>(key);
-            c.seed = std::get<2>(key);
+            c.ts_class = std::get<2>(key);
+            c.seed = std::get<3>(key);
             auto w = warps_of.find(key);
             if (w != warps_of.end()) c.warps = w->second;
             index[key] = b->classes.size();
@@ -298,7 +316,7 @@ int enqueue_chunk(ga_batch *b, uint32_t gens)
     b->launches += 1;
     for (uint32_t dg = 0; dg < gens; ++dg) {
         for (const auto &c : b->classes) {
-            const ga::BatchKernel k = ga::pick(c.island_size, c.sw_class, c.warps);
+            const ga::BatchKernel k = ga::pick(c.island_size, c.sw_class, c.ts_class, c.warps);
             if (!k) return GA_EUNSUPPORTED;
             ga::BatchArgs a;
             a.runs = b->d_runs;
@@ -406,7 +424,8 @@ int ga_batch_add(ga_batch *b, ga_run *run)
 {
     if (!b || !run) return GA_EINVAL;
     if (std::find(b->runs.begin(), b->runs.end(), run) != b->runs.end()) return GA_EINVAL;
-    if (!ga::pick(run->cfg.island_size, ga::sw_class(run->surface_words), 8)) return GA_EUNSUPPORTED;
+    if (!ga::pick(run->cfg.island_size, ga::sw_class(run->surface_words), 0, 8))
+        return GA_EUNSUPPORTED;
     if (run->generation + 1 > 0xFFFFFFFFull) return GA_EINVAL;
     // the run's own queued work must be done before the batch stream touches its buffers
     if (cudaStreamSynchronize(run->stream) != cudaSuccess) return GA_ECUDA;

@@ -12,7 +12,9 @@ import numpy as np
 
 from .workloads import RunShape
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libga.so")
+# The library built in-tree; PAPER_2405_03605_GB300_LIB may name another build of it.
+LIB_PATH = os.environ.get("PAPER_2405_03605_GB300_LIB") or os.path.join(
+    os.path.dirname(os.path.abspath(__file__)), "libga.so")
 
 GA_OK = 0
 STEADY, TILTED, HYBRID = 0, 1, 2

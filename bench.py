@@ -143,6 +143,13 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
+# DRAM bytes (read + write) of one island_step_kernel<32,2,5> launch on the 512x1024x32 grid,
+# from the ncu capture summarised in profiles/island_step_kernel_512x1024x32_16B.md; it
+# describes that kernel build only.
+ISLAND_STEP_TRAFFIC = {"kernel": "island_step_kernel<32,2,5>", "bytes": 494.2e6,
+                       "rows": 512, "cols": 1024, "island_size": 32}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -298,6 +305,9 @@ def run_ours(args, rank, world, local):
     achieved = bytes_per_launch / avg_launch_s / 1e9
     peak, peak_kind = measured_peaks()
     mrca_ms = statistics.mean(a.elapsed_time(b) for a, b in mrca_pairs)
+    same_shape = (args.rows, args.cols, shs[0].island_size) == (
+        ISLAND_STEP_TRAFFIC["rows"], ISLAND_STEP_TRAFFIC["cols"], ISLAND_STEP_TRAFFIC["island_size"])
+    traffic = ISLAND_STEP_TRAFFIC["bytes"] if same_shape else None
 
     e2e = None
     if not args.no_e2e:
@@ -324,8 +334,8 @@ def run_ours(args, rank, world, local):
         "config": {**workload_config(args, shs[0]),
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "island_step_kernel<32,2>",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": ISLAND_STEP_TRAFFIC["kernel"],
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "bytes_per_launch": bytes_per_launch,
                      "avg_launch_us": avg_launch_s * 1e6},

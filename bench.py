@@ -143,11 +143,24 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
-# DRAM bytes (read + write) of one island_step_kernel<32,2,5> launch on the 512x1024x32 grid,
-# from the ncu capture summarised in profiles/island_step_kernel_512x1024x32_16B.md; it
-# describes that kernel build only.
+# DRAM bytes (read + write) of one island_step_kernel<32,2,5> launch on the 512x1024x32 grid:
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this kernel build.
 ISLAND_STEP_TRAFFIC = {"kernel": "island_step_kernel<32,2,5>", "bytes": 494.2e6,
                        "rows": 512, "cols": 1024, "island_size": 32}
+
+
+def aggregate_replicas(elapsed_ms, agent_gens, world, device="cpu"):
+    """Whole-job figures over independent replicas (one per rank): the slowest rank's time
+    and the sum of all ranks' agent-generations.  With world == 1 the inputs come back."""
+    if world <= 1:
+        return float(elapsed_ms), float(agent_gens)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(agent_gens)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
 
 
 def measured_peaks():
@@ -287,11 +300,9 @@ def run_ours(args, rank, world, local):
         r.sync()
     launches = sum(r.launches for r in runs) - launches0
     elapsed_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    agent_gens = args.steps * sum(s.n_agents * args.gens for s in shs) * world
+    local_agent_gens = args.steps * sum(s.n_agents * args.gens for s in shs)
+    elapsed_ms, agent_gens = aggregate_replicas(elapsed_ms, local_agent_gens, world,
+                                                device="cuda")
     value = agent_gens / (elapsed_ms / 1000.0)
 
     # roofline of the island-step kernel: one launch = one generation of one run (migration

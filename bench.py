@@ -320,6 +320,15 @@ def run_ours(args, rank, world, local):
         ISLAND_STEP_TRAFFIC["rows"], ISLAND_STEP_TRAFFIC["cols"], ISLAND_STEP_TRAFFIC["island_size"])
     traffic = ISLAND_STEP_TRAFFIC["bytes"] if same_shape else None
 
+    # Sec. 3 treatment contrast from the last step's MRCA bounds: mean time since divergence
+    # bounded below by T - hi (purifying-only runs should keep deeper genealogies)
+    contrast = {}
+    with torch.cuda.stream(stream):
+        for sh, (lo, hi) in zip(shs, outs):
+            depth = (args.gens - hi.to(torch.int64)).double().mean().item()
+            contrast["adaptive" if sh.p_ben > 0 else "purifying"] = depth
+    contrast["unit"] = "generations (mean over sampled pairs of T - hi)"
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(args, shs, ids_h, world)
@@ -350,7 +359,11 @@ def run_ours(args, rank, world, local):
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "bytes_per_launch": bytes_per_launch,
                      "avg_launch_us": avg_launch_s * 1e6},
-        "mrca_ms_per_run": mrca_ms,
+        "mrca": {"ms_per_run": mrca_ms, "pairs": pairs, "bytes_written": 8 * pairs,
+                 "achieved": 8 * pairs / (mrca_ms / 1000.0) / 1e9, "peak": peak, "unit": "GB/s",
+                 "frac": 8 * pairs / (mrca_ms / 1000.0) / 1e9 / peak,
+                 "note": "all four MRCA kernels per call; bound by the (lo, hi) output writes"},
+        "treatment_contrast": contrast,
         "batched_vs_serial": batched,
         **({"serving": served} if served is not None else {}),
         **({"variants": variants} if variants is not None else {}),

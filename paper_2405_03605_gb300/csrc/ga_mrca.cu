@@ -6,8 +6,9 @@
 //                      largest rank that landed on it (atomicMax of rank + 1).
 //   2. order_kernel  : sort the occupied sites by rank (one block, S <= 256): r_1 < ... < r_m.
 //   3. pack_kernel   : gather each sampled agent's differentiae in rank order into a bit
-//                      string (differentia i at bits [i*b, i*b + b)), 8 words per agent.
-//   4. pair_kernel   : one warp per row i; for each j > i the first set bit of
+//                      string (differentia i at bits [i*b, i*b + b)), 8 words per agent; one
+//                      warp per agent, one warp OR-reduction per packed word.
+//   4. pair_kernel   : one thread per pair (i, j), j > i; the first set bit of
 //                      packed[i] ^ packed[j] gives the first mismatching rank index i*,
 //                      from which hi = r_{i*} and lo = r_{i*-K} + 1 (0 if i* <= K); with no
 //                      mismatch hi = T, lo = r_{m-K+1} + 1 (0 if m < K).
@@ -81,6 +82,9 @@ __global__ void order_kernel(const uint32_t *__restrict__ holder, uint32_t *__re
     if (k == 0) meta[0] = static_cast<uint32_t>(m);
 }
 
+// One warp per sampled agent: lanes 0..7 hold the agent's surface words; for packed word w,
+// lane l gathers differentia index w * (32/b) + l (site order[i], fetched from the lane that
+// holds its surface word) and one warp OR-reduction assembles the word.
 __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_words,
                             uint32_t n_agents, const uint32_t *__restrict__ ids, uint32_t n,
                             const uint32_t *__restrict__ order, const uint32_t *__restrict__ meta,
@@ -91,86 +95,92 @@ __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_wo
     const uint32_t m = meta[0];
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ord[i] = order[i];
     __syncthreads();
-    const uint32_t a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n) return;
-    uint32_t out[kPackWords] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (a >= n) return;  // whole warps
     const uint32_t id = ids[a];
+    uint32_t word_out = 0;
     if (id >= n_agents) {
-        atomicCAS(status, GA_OK, GA_EINVAL);
+        if (lane == 0) atomicCAS(status, GA_OK, GA_EINVAL);
     } else {
         const uint32_t *rec = pop + static_cast<size_t>(id) * record_words;
-        if (rec[1] != T) atomicCAS(status, GA_OK, GA_ESTATE);
-        uint32_t surf[kPackWords];
-#pragma unroll
-        for (uint32_t w = 0; w < kPackWords; ++w) surf[w] = (2u + w < record_words) ? rec[2 + w] : 0u;
-        const uint32_t mask = (1u << bits) - 1u;
-        for (uint32_t i = 0; i < m; ++i) {
-            const uint32_t pos = ord[i] * bits;
-            uint32_t word = 0;
-#pragma unroll
-            for (uint32_t w = 0; w < kPackWords; ++w)
-                if (w == (pos >> 5)) word = surf[w];
-            const uint32_t d = (word >> (pos & 31u)) & mask;
-            const uint32_t dst = i * bits;
-#pragma unroll
-            for (uint32_t w = 0; w < kPackWords; ++w)
-                if (w == (dst >> 5)) out[w] |= d << (dst & 31u);
+        if (lane == 0 && rec[1] != T) atomicCAS(status, GA_OK, GA_ESTATE);
+        const uint32_t surf = (lane < kPackWords && 2u + lane < record_words) ? rec[2 + lane] : 0u;
+        const uint32_t per = 32u / bits, mask = (1u << bits) - 1u;
+        const uint32_t pw = (m * bits + 31u) >> 5;
+        for (uint32_t w = 0; w < pw; ++w) {
+            const uint32_t i = w * per + lane;
+            const uint32_t pos = (lane < per && i < m) ? ord[i] * bits : 0u;
+            const uint32_t sw = __shfl_sync(0xffffffffu, surf, static_cast<int>(pos >> 5));
+            const uint32_t v = (lane < per && i < m) ? ((sw >> (pos & 31u)) & mask) << (lane * bits) : 0u;
+            const uint32_t full = __reduce_or_sync(0xffffffffu, v);
+            if (lane == w) word_out = full;
         }
     }
-    uint4 *o = reinterpret_cast<uint4 *>(packed + static_cast<size_t>(a) * kPackWords);
-    o[0] = make_uint4(out[0], out[1], out[2], out[3]);
-    o[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    if (lane < kPackWords) packed[static_cast<size_t>(a) * kPackWords + lane] = word_out;
 }
 
+// One thread per pair: block (x, y) covers row i = y and columns j = i + 1 + 256 x + t.  The
+// first set bit of packed[i] ^ packed[j] gives the first mismatching rank index i*.
 __global__ void __launch_bounds__(kPairThreads)
 pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__restrict__ ranks_g,
             const uint32_t *__restrict__ meta, uint32_t bits, uint32_t K, uint32_t T,
             uint32_t *__restrict__ lo, uint32_t *__restrict__ hi)
 {
     __shared__ uint32_t ranks[256];
+    __shared__ uint32_t mine[kPackWords];
     const uint32_t m = meta[0];
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ranks[i] = ranks_g[i];
-    __syncthreads();
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (row >= n) return;
     const uint32_t pw = (m * bits + 31u) >> 5;
-    uint32_t mine[kPackWords];
-    const uint4 *pi = reinterpret_cast<const uint4 *>(packed + static_cast<size_t>(row) * kPackWords);
-    const uint4 a0 = pi[0], a1 = pi[1];
-    mine[0] = a0.x; mine[1] = a0.y; mine[2] = a0.z; mine[3] = a0.w;
-    mine[4] = a1.x; mine[5] = a1.y; mine[6] = a1.z; mine[7] = a1.w;
-    const uint32_t none_hi = T;
-    const uint32_t none_lo = m >= K ? ranks[m - K] + 1u : 0u;
-    const size_t base = static_cast<size_t>(row) * (2ull * n - row - 1ull) / 2ull;
-    for (uint32_t j = row + 1u + lane; j < n; j += 32u) {
-        const uint4 *pj = reinterpret_cast<const uint4 *>(packed + static_cast<size_t>(j) * kPackWords);
-        const uint4 b0 = __ldg(&pj[0]);
-        uint32_t x[kPackWords];
-        x[0] = b0.x ^ mine[0]; x[1] = b0.y ^ mine[1]; x[2] = b0.z ^ mine[2]; x[3] = b0.w ^ mine[3];
-        if (pw > 4u) {
-            const uint4 b1 = __ldg(&pj[1]);
-            x[4] = b1.x ^ mine[4]; x[5] = b1.y ^ mine[5]; x[6] = b1.z ^ mine[6]; x[7] = b1.w ^ mine[7];
-        } else {
-            x[4] = x[5] = x[6] = x[7] = 0u;
-        }
-        uint32_t first_bit = 0xFFFFFFFFu;
+    for (uint32_t row = blockIdx.y; row < n; row += gridDim.y) {
+        const uint32_t j0 = row + 1u + blockIdx.x * kPairThreads;
+        if (j0 >= n) continue;  // uniform across the block
+        if (threadIdx.x < kPackWords) mine[threadIdx.x] = packed[static_cast<size_t>(row) * kPackWords + threadIdx.x];
+        __syncthreads();
+        const uint32_t j = j0 + threadIdx.x;
+        if (j < n) {
+            const uint4 *pj = reinterpret_cast<const uint4 *>(packed + static_cast<size_t>(j) * kPackWords);
+            const uint4 b0 = __ldg(&pj[0]);
+            uint32_t x[kPackWords];
+            x[0] = b0.x ^ mine[0]; x[1] = b0.y ^ mine[1]; x[2] = b0.z ^ mine[2]; x[3] = b0.w ^ mine[3];
+            if (pw > 4u) {
+                const uint4 b1 = __ldg(&pj[1]);
+                x[4] = b1.x ^ mine[4]; x[5] = b1.y ^ mine[5]; x[6] = b1.z ^ mine[6]; x[7] = b1.w ^ mine[7];
+            } else {
+                x[4] = x[5] = x[6] = x[7] = 0u;
+            }
+            uint32_t first_bit = 0xFFFFFFFFu;
 #pragma unroll
-        for (int w = kPackWords - 1; w >= 0; --w)
-            if (x[w] != 0u) first_bit = 32u * w + (__ffs(x[w]) - 1u);
-        uint32_t l, h;
-        if (first_bit == 0xFFFFFFFFu) {
-            h = none_hi;
-            l = none_lo;
-        } else {
-            const uint32_t istar = first_bit / bits;  // 0-based index of the first mismatch
-            h = ranks[istar];
-            l = istar >= K ? ranks[istar - K] + 1u : 0u;
+            for (int w = kPackWords - 1; w >= 0; --w)
+                if (x[w] != 0u) first_bit = 32u * w + (__ffs(x[w]) - 1u);
+            uint32_t l, h;
+            if (first_bit == 0xFFFFFFFFu) {
+                h = T;
+                l = m >= K ? ranks[m - K] + 1u : 0u;
+            } else {
+                const uint32_t istar = first_bit / bits;  // 0-based index of the first mismatch
+                h = ranks[istar];
+                l = istar >= K ? ranks[istar - K] + 1u : 0u;
+            }
+            const size_t p = static_cast<size_t>(row) * (2ull * n - row - 1ull) / 2ull + (j - row - 1u);
+            __stcs(&lo[p], l);
+            __stcs(&hi[p], h);
         }
-        const size_t p = base + (j - row - 1u);
-        __stcs(&lo[p], l);
-        __stcs(&hi[p], h);
+        __syncthreads();  // `mine` is rewritten for the next row
     }
+}
+
+// pack + pair launches shared by the allocating and the fixed-scratch entry points
+void launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, uint32_t n_agents,
+                           const uint32_t *d_ids, uint32_t n, const uint32_t *order,
+                           const uint32_t *ranks, const uint32_t *meta, uint32_t bits, uint32_t K,
+                           uint32_t T, uint32_t *packed, uint32_t *d_lo, uint32_t *d_hi,
+                           int *status, cudaStream_t stream)
+{
+    pack_kernel<<<(n + 7u) / 8u, 256, 0, stream>>>(pop, record_words, n_agents, d_ids, n, order,
+                                                   meta, bits, T, packed, status);
+    const dim3 grid((n + kPairThreads - 1) / kPairThreads, n < 65535u ? n : 65535u);
+    pair_kernel<<<grid, kPairThreads, 0, stream>>>(packed, n, ranks, meta, bits, K, T, d_lo, d_hi);
 }
 
 uint32_t margin(uint32_t bits)
@@ -206,14 +216,11 @@ cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t
     }
     order_kernel<<<1, 256, 0, run->stream>>>(l.holder, l.order, l.ranks, l.meta, S);
     run->launches += 1;
-    pack_kernel<<<(n + 127u) / 128u, 128, 0, run->stream>>>(
-        reinterpret_cast<const uint32_t *>(run->pop[run->cur]), run->record_bytes / 4u,
-        run->n_agents, d_ids, n, l.order, l.meta, b, T, l.packed, run->d_status);
-    run->launches += 1;
-    const uint32_t rows_per_block = kPairThreads / 32;
-    pair_kernel<<<(n + rows_per_block - 1) / rows_per_block, kPairThreads, 0, run->stream>>>(
-        l.packed, n, l.ranks, l.meta, b, margin(b), T, d_lo, d_hi);
-    run->launches += 1;
+    launch_pack_and_pairs(reinterpret_cast<const uint32_t *>(run->pop[run->cur]),
+                          run->record_bytes / 4u, run->n_agents, d_ids, n, l.order, l.ranks,
+                          l.meta, b, margin(b), T, l.packed, d_lo, d_hi, run->d_status,
+                          run->stream);
+    run->launches += 2;
     return cudaGetLastError();
 }
 
@@ -305,13 +312,9 @@ extern "C" int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_byt
         rank_kernel<<<blocks, 256, 0, st>>>(l.holder, curation, log2_sites, S, generation);
     }
     order_kernel<<<1, 256, 0, st>>>(l.holder, l.order, l.ranks, l.meta, S);
-    pack_kernel<<<(n + 127u) / 128u, 128, 0, st>>>(static_cast<const uint32_t *>(d_records),
-                                                   record_bytes / 4u, n_agents, d_agent_ids, n,
-                                                   l.order, l.meta, b, generation, l.packed,
-                                                   status);
-    const uint32_t rows_per_block = kPairThreads / 32;
-    pair_kernel<<<(n + rows_per_block - 1) / rows_per_block, kPairThreads, 0, st>>>(
-        l.packed, n, l.ranks, l.meta, b, margin(b), generation, d_lo, d_hi);
+    launch_pack_and_pairs(static_cast<const uint32_t *>(d_records), record_bytes / 4u, n_agents,
+                          d_agent_ids, n, l.order, l.ranks, l.meta, b, margin(b), generation,
+                          l.packed, d_lo, d_hi, status, st);
     if (cudaGetLastError() != cudaSuccess) return GA_ECUDA;
     int device_status = GA_OK;
     if (cudaMemcpyAsync(&device_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) !=

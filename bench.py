@@ -52,6 +52,8 @@ def parse_args():
     p.add_argument("--serve-requests", type=int, default=200)
     p.add_argument("--variants", action="store_true")
     p.add_argument("--variant-gens", type=int, default=1000)
+    p.add_argument("--paper-treatments", action="store_true")
+    p.add_argument("--treatment-gens", type=int, default=10000)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -337,6 +339,7 @@ def run_ours(args, rank, world, local):
         batched = measure_batch(args, rank)
     served = measure_serve(args) if args.serve and rank == 0 else None
     variants = measure_variants(args) if args.variants and rank == 0 else None
+    treatments = measure_treatments(args) if args.paper_treatments and rank == 0 else None
 
     for r in runs:
         r.close()
@@ -367,6 +370,7 @@ def run_ours(args, rank, world, local):
         "batched_vs_serial": batched,
         **({"serving": served} if served is not None else {}),
         **({"variants": variants} if variants is not None else {}),
+        **({"paper_treatments": treatments} if treatments is not None else {}),
         "gpu_launches": launches,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -477,6 +481,45 @@ def measure_variants(args):
                             "hbm_frac": rate * b_alg / 1e9 / peak})
                 r.close()
     return {"agents": 4194304, "generations": gens, "runs": out}
+
+
+def measure_treatments(args):
+    """The paper's own treatments (Sec. 3) on the 512x1024x32 grid: float fitness, 33% of
+    births lose a normally distributed amount (purifying-only), plus 0.3% that gain one
+    (adaptive); each run from founders for --treatment-gens generations, then MRCA bounds over
+    4,096 sampled agents.  Reports agent-generations/s and the mean MRCA depth (T - hi)."""
+    import numpy as np
+    import torch
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import (PAPER_FITNESS_ADAPTIVE,
+                                                  PAPER_FITNESS_PURIFYING, sample_agent_ids)
+
+    gens = args.treatment_gens
+    stream = torch.cuda.Stream()
+    out = {"generations": gens}
+    for name, sh in (("purifying", PAPER_FITNESS_PURIFYING), ("adaptive", PAPER_FITNESS_ADAPTIVE)):
+        r = ga.Run(sh, stream=stream)
+        r.step(3)
+        r.reset()
+        ids = torch.from_numpy(sample_agent_ids(sh.n_agents, 4096, seed=7).view(np.int32))
+        with torch.cuda.stream(stream):
+            ids = ids.cuda()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.step(gens)
+        e1.record(stream)
+        lo, hi = r.mrca_bounds_device(ids)
+        r.sync()
+        ms = e0.elapsed_time(e1)
+        with torch.cuda.stream(stream):
+            depth = (gens - hi.to(torch.int64)).double().mean().item()
+            fit = r.snapshot_device()[:, 0:4].contiguous().view(torch.float32)
+            mean_fit = fit.double().mean().item()
+        stream.synchronize()
+        out[name] = {"agent_gens_per_s": sh.n_agents * gens / (ms / 1000.0),
+                     "mean_mrca_depth": depth, "mean_fitness": mean_fit}
+        r.close()
+    return out
 
 
 def measure_serve(args):

@@ -58,6 +58,14 @@ extern "C" {
 
 #define GA_SYNC 0u /* synchronous generations: deterministic, bit-exact                  */
 
+/* Genome model: what the first record word means and how it mutates. */
+#define GA_MODEL_TRAIT 0u   /* int32 trait; +1 with p_ben, -1 with p_del                     */
+#define GA_MODEL_FITNESS 1u /* IEEE float fitness (Sec. 3 treatments): -/+ effect_scale * |z|
+                               with p_del / p_ben, z a standard normal deviate (Box-Muller in
+                               single precision, correctly rounded operations only, from
+                               Philox words 0 and 1 of counter (g, island, slot | 3 << 16,
+                               run_id)); tournaments compare fitness as floats              */
+
 typedef struct ga_run ga_run;
 
 typedef struct ga_config {
@@ -71,12 +79,13 @@ typedef struct ga_config {
     uint32_t mode;              /* GA_SYNC                                                    */
     uint64_t seed;              /* Philox key = (low 32 bits, high 32 bits)                   */
     uint32_t run_id;            /* fourth Philox counter word: distinct runs draw disjointly  */
-    uint32_t reserved;          /* must be 0                                                  */
+    uint32_t model;             /* GA_MODEL_TRAIT / GA_MODEL_FITNESS                          */
     void *stream;               /* cudaStream_t for all of this run's GPU work (NULL: default) */
+    double effect_scale;        /* GA_MODEL_FITNESS: scale of the normal mutation amount > 0  */
 } ga_config;
 
 /* Fill *cfg with the 32x32-torus defaults: N = 32, n = 5, p_ben = p_del = 0.01, S = 64,
-   b = 1, steady, sync, seed 42, run_id 0, default stream. */
+   b = 1, steady, sync, trait model, seed 42, run_id 0, default stream, effect_scale 1. */
 int ga_config_default(ga_config *cfg);
 
 /* Check a configuration without touching the GPU.  GA_EINVAL: invalid;
@@ -179,7 +188,7 @@ int ga_mrca_bounds_device(ga_run *run, const uint32_t *d_agent_ids, uint32_t n,
  * A run belongs to at most one batch at a time.  Call ga_batch_sync before any per-run call
  * on a member (ga_snapshot, ga_mrca_bounds, ga_step, ga_reset, ga_load, ...); a member whose
  * generation or buffer changed through such calls is picked up by the next ga_batch_step.  Member runs may have different shapes, mutation rates, tournament
- * sizes, curation policies, seeds and migration policies; island sizes 8..64.
+ * sizes, curation policies, seeds and migration policies; island sizes 8..64, trait model.
  */
 typedef struct ga_batch ga_batch;
 

@@ -10,6 +10,11 @@ from .oracle import (  # noqa: F401
     STEADY,
     TILTED,
     HYBRID,
+    MODEL_TRAIT,
+    MODEL_FITNESS,
+    normal,
+    unit_log,
+    turn_cos,
     philox4x32_10,
     site,
     site_table,

@@ -15,7 +15,10 @@ OUT = os.path.join(OUT_DIR, "libga_oracle.so")
 
 
 def _compile(extra):
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *extra, SRC, "-o", OUT, "-lm"]
+    # -ffp-contract=off: every float operation is rounded on its own (no fused multiply-add),
+    # as the normal-deviate arithmetic requires
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *extra, SRC,
+           "-o", OUT, "-lm"]
     return subprocess.run(cmd, capture_output=True, text=True)
 
 

@@ -67,6 +67,7 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
 /* Draw purposes: the third counter word is (slot | purpose << 16). */
 #define ORC_PURPOSE_BIRTH   1u
 #define ORC_PURPOSE_FOUNDER 2u
+#define ORC_PURPOSE_MUTATE  3u
 
 static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t slot, uint32_t purpose,
                  uint32_t run_id, uint32_t out[4])
@@ -74,6 +75,82 @@ static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t slot, uint32_
     uint32_t ctr[4] = {c0, c1, slot | (purpose << 16), run_id};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     orc_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Normal deviates for the float-fitness treatments of Sec. 3 ("decreased / increased     */
+/* fitness by a normally-distributed amount"), by the Box-Muller transform,               */
+/* z = sqrt(-2 ln u1) cos(2 pi u2), in IEEE single precision from correctly rounded       */
+/* operations only (+, -, *, /, sqrt; this file is compiled without FMA contraction), so   */
+/* that any other implementation performing the same operations gets the same bits:       */
+/*   ln x, x in (0, 1]: x = m 2^e with m in [0.5, 1) read from the float's bits;          */
+/*     ln m = 2 atanh(s), s = (m - 1)/(m + 1), by the series 2 s (1 + s^2/3 + ... + s^12/13) */
+/*     in Horner form; ln x = e ln 2 + ln m.                                               */
+/*   cos(2 pi k / 2^24): quadrant q = k >> 22, angle a = (k mod 2^22) 2^-22 (pi/2); the     */
+/*     Taylor series of cos a (to a^14) and sin a (to a^15) in Horner form, then           */
+/*     cos, -sin, -cos, sin for q = 0, 1, 2, 3.                                             */
+/*   u1 = (k1 + 1) 2^-24 in (0, 1], k1 = top 24 bits of word a; k = top 24 bits of word b. */
+/* ------------------------------------------------------------------------------------ */
+static float unit_log(float x)
+{
+    uint32_t bits;
+    memcpy(&bits, &x, 4);
+    const int e = (int)((bits >> 23) & 0xFFu) - 126;
+    const uint32_t mbits = (bits & 0x007FFFFFu) | 0x3F000000u;
+    float m;
+    memcpy(&m, &mbits, 4);
+    const float s = (m - 1.0f) / (m + 1.0f);
+    const float t = s * s;
+    float p = (float)(1.0 / 13.0);
+    p = p * t + (float)(1.0 / 11.0);
+    p = p * t + (float)(1.0 / 9.0);
+    p = p * t + (float)(1.0 / 7.0);
+    p = p * t + (float)(1.0 / 5.0);
+    p = p * t + (float)(1.0 / 3.0);
+    p = p * t + 1.0f;
+    const float ln_m = (2.0f * s) * p;
+    return (float)e * (float)0.69314718055994530942 + ln_m;
+}
+
+static float turn_cos(uint32_t k)
+{
+    const uint32_t q = (k >> 22) & 3u;
+    const float a = ((float)(k & 0x3FFFFFu) * (float)(1.0 / 4194304.0)) *
+                    (float)(3.14159265358979323846 / 2.0);
+    const float a2 = a * a;
+    float c = -(float)(1.0 / 87178291200.0); /* -1/14! */
+    c = c * a2 + (float)(1.0 / 479001600.0); /*  1/12! */
+    c = c * a2 - (float)(1.0 / 3628800.0);   /* -1/10! */
+    c = c * a2 + (float)(1.0 / 40320.0);     /*  1/8!  */
+    c = c * a2 - (float)(1.0 / 720.0);       /* -1/6!  */
+    c = c * a2 + (float)(1.0 / 24.0);        /*  1/4!  */
+    c = c * a2 - 0.5f;                       /* -1/2!  */
+    c = c * a2 + 1.0f;
+    float sn = -(float)(1.0 / 1307674368000.0); /* -1/15! */
+    sn = sn * a2 + (float)(1.0 / 6227020800.0); /*  1/13! */
+    sn = sn * a2 - (float)(1.0 / 39916800.0);   /* -1/11! */
+    sn = sn * a2 + (float)(1.0 / 362880.0);     /*  1/9!  */
+    sn = sn * a2 - (float)(1.0 / 5040.0);       /* -1/7!  */
+    sn = sn * a2 + (float)(1.0 / 120.0);        /*  1/5!  */
+    sn = sn * a2 - (float)(1.0 / 6.0);          /* -1/3!  */
+    sn = sn * a2 + 1.0f;
+    sn = sn * a;
+    switch (q) {
+    case 0: return c;
+    case 1: return -sn;
+    case 2: return -c;
+    default: return sn;
+    }
+}
+
+float orc_unit_log(float x) { return unit_log(x); }
+float orc_turn_cos(uint32_t k) { return turn_cos(k); }
+
+float orc_normal(uint32_t a, uint32_t b)
+{
+    const float u1 = (float)((a >> 8) + 1u) * (float)(1.0 / 16777216.0);
+    const float r = sqrtf(-2.0f * unit_log(u1));
+    return r * turn_cos(b >> 8);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -192,7 +269,15 @@ typedef struct {
     uint64_t seed;
     uint32_t run_id;
     uint32_t threads;           /* worker threads for the per-island loops (0 or 1: one) */
+    uint32_t model;             /* ORC_MODEL_TRAIT or ORC_MODEL_FITNESS                  */
+    double effect_scale;        /* ORC_MODEL_FITNESS: mutation amount = scale * |z|      */
 } orc_config;
+
+/* Genome models.  TRAIT: int32 trait, +1 / -1 mutations.  FITNESS (Sec. 3 treatments): the
+   first word is an IEEE float fitness; a deleterious mutation subtracts, a beneficial one
+   adds, effect_scale * |z| with z a standard normal deviate drawn from
+   Philox((g, island, slot | MUTATE << 16, run)) words 0 and 1. */
+enum { ORC_MODEL_TRAIT = 0, ORC_MODEL_FITNESS = 1 };
 
 typedef struct {
     orc_config cfg;
@@ -236,6 +321,9 @@ int orc_validate(const orc_config *c)
     if (c->curation > ORC_HYBRID) return -1;
     if ((uint64_t)c->surface_sites * c->differentia_bits > 256) return -1;
     if ((uint64_t)c->rows * c->cols * c->island_size > 0xFFFFFFFFull) return -1;
+    if (c->model > ORC_MODEL_FITNESS) return -1;
+    if (c->model == ORC_MODEL_FITNESS && !(c->effect_scale > 0.0 && c->effect_scale < 1e30))
+        return -1;
     return 0;
 }
 
@@ -404,7 +492,16 @@ void orc_reproduce(orc_state *st, uint32_t *parent_slots)
                 uint32_t word = i < 4 ? w[0] : w[1];
                 uint32_t byte = (word >> (8 * (i % 4))) & 0xFFu;
                 uint32_t idx = (byte * N) >> 8;
-                if (i == 0 || st->trait[base + idx] > st->trait[base + best]) best = idx;
+                int better;
+                if (c->model == ORC_MODEL_FITNESS) {
+                    float fi, fb;
+                    memcpy(&fi, &st->trait[base + idx], 4);
+                    memcpy(&fb, &st->trait[base + best], 4);
+                    better = fi > fb;
+                } else {
+                    better = st->trait[base + idx] > st->trait[base + best];
+                }
+                if (i == 0 || better) best = idx;
             }
             if (parent_slots) parent_slots[base + j] = best;
             /* copy */
@@ -413,10 +510,23 @@ void orc_reproduce(orc_state *st, uint32_t *parent_slots)
                        st->counter, st->surface, parent);
             /* mutate */
             uint32_t x = w[2];
-            if (x < st->theta_del)
+            int del = x < st->theta_del;
+            int ben = !del && x - st->theta_del < st->theta_ben;
+            if (c->model == ORC_MODEL_FITNESS) {
+                if (del || ben) {
+                    uint32_t mw[4];
+                    draw(c->seed, g, isl, j, ORC_PURPOSE_MUTATE, c->run_id, mw);
+                    const float amount = (float)c->effect_scale * fabsf(orc_normal(mw[0], mw[1]));
+                    float f;
+                    memcpy(&f, &st->trait2[child], 4);
+                    f = del ? f - amount : f + amount;
+                    memcpy(&st->trait2[child], &f, 4);
+                }
+            } else if (del) {
                 st->trait2[child] = (int32_t)((uint32_t)st->trait2[child] - 1u);
-            else if (x - st->theta_del < st->theta_ben)
+            } else if (ben) {
                 st->trait2[child] = (int32_t)((uint32_t)st->trait2[child] + 1u);
+            }
             /* hstrat deposit for the elapsed generation */
             int64_t site = orc_site(c->curation, c->surface_sites, st->counter2[child]);
             if (site >= 0) {

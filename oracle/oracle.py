@@ -5,6 +5,7 @@ import numpy as np
 from .build import build
 
 STEADY, TILTED, HYBRID = 0, 1, 2
+MODEL_TRAIT, MODEL_FITNESS = 0, 1
 
 _lib = None
 
@@ -55,6 +56,12 @@ def _load():
     lib.orc_mrca_bounds.argtypes = [C.c_void_p, C.c_uint32, u32p, C.c_uint32, C.c_uint32,
                                     C.c_uint32, C.c_uint32, C.c_uint64, u32p, u32p]
     lib.orc_mrca_bounds.restype = C.c_int
+    lib.orc_normal.argtypes = [C.c_uint32, C.c_uint32]
+    lib.orc_normal.restype = C.c_float
+    lib.orc_unit_log.argtypes = [C.c_float]
+    lib.orc_unit_log.restype = C.c_float
+    lib.orc_turn_cos.argtypes = [C.c_uint32]
+    lib.orc_turn_cos.restype = C.c_float
     lib.orc_openmp_enabled.argtypes = []
     lib.orc_openmp_enabled.restype = C.c_int
     _lib = lib
@@ -70,6 +77,7 @@ class OracleConfig(C.Structure):
         ("surface_sites", C.c_uint32), ("differentia_bits", C.c_uint32),
         ("curation", C.c_uint32), ("migrate_every", C.c_uint32),
         ("seed", C.c_uint64), ("run_id", C.c_uint32), ("threads", C.c_uint32),
+        ("model", C.c_uint32), ("effect_scale", C.c_double),
     ]
 
 
@@ -134,6 +142,20 @@ def mrca_bounds(records, ids, policy, S, b, T):
     return lo, hi
 
 
+def normal(a, b):
+    """Standard normal deviate from two 32-bit words (Box-Muller in IEEE single)."""
+    return float(_load().orc_normal(a, b))
+
+
+def unit_log(x):
+    return float(_load().orc_unit_log(x))
+
+
+def turn_cos(k):
+    """cos(2 pi k / 2^24) for a 24-bit k."""
+    return float(_load().orc_turn_cos(k))
+
+
 def openmp_enabled():
     return bool(_load().orc_openmp_enabled())
 
@@ -143,11 +165,11 @@ class OracleRun:
 
     def __init__(self, rows, cols, island_size=32, tournament_size=5, p_ben=0.01, p_del=0.01,
                  surface_sites=64, differentia_bits=1, curation=STEADY, migrate_every=1,
-                 seed=42, run_id=0, threads=1):
+                 seed=42, run_id=0, threads=1, model=MODEL_TRAIT, effect_scale=1.0):
         self._lib = _load()
         self.cfg = OracleConfig(rows, cols, island_size, tournament_size, p_ben, p_del,
                                 surface_sites, differentia_bits, curation, migrate_every,
-                                seed, run_id, threads)
+                                seed, run_id, threads, model, effect_scale)
         self._st = self._lib.orc_create(C.byref(self.cfg))
         if not self._st:
             raise ValueError("invalid oracle config")
@@ -197,6 +219,9 @@ class OracleRun:
 
     def traits(self):
         return self.snapshot()[:, 0:4].copy().view(np.int32).reshape(-1)
+
+    def fitness(self):
+        return self.snapshot()[:, 0:4].copy().view(np.float32).reshape(-1)
 
     def counters(self):
         return self.snapshot()[:, 4:8].copy().view(np.uint32).reshape(-1)

@@ -51,10 +51,12 @@ int check_config(const ga_config *c)
     if (c->curation > GA_HYBRID) return GA_EINVAL;
     if (c->surface_sites < (c->curation == GA_HYBRID ? 8u : 4u)) return GA_EINVAL;
     if (static_cast<uint64_t>(c->surface_sites) * b > 256u) return GA_EINVAL;
-    if (c->mode != GA_SYNC || c->reserved != 0) return GA_EINVAL;
+    if (c->mode != GA_SYNC || c->model > GA_MODEL_FITNESS) return GA_EINVAL;
+    if (c->model == GA_MODEL_FITNESS && !(c->effect_scale > 0.0 && c->effect_scale < 1e30))
+        return GA_EINVAL;
     const uint64_t agents = static_cast<uint64_t>(c->rows) * c->cols * c->island_size;
     if (agents > 0xFFFFFFFFull) return GA_EINVAL;
-    if (!ga::step_supported(c->island_size, surface_words_of(c))) return GA_EUNSUPPORTED;
+    if (!ga::step_supported(c->island_size, surface_words_of(c), c->model)) return GA_EUNSUPPORTED;
     return GA_OK;
 }
 
@@ -103,7 +105,9 @@ int ga_config_default(ga_config *cfg)
     cfg->mode = GA_SYNC;
     cfg->seed = 42;
     cfg->run_id = 0;
+    cfg->model = GA_MODEL_TRAIT;
     cfg->stream = nullptr;
+    cfg->effect_scale = 1.0;
     return GA_OK;
 }
 

@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
         s_r.n_gens = 1;
         s_r.migrate = d.per_neighbor && (d.every_k == 1u || s_r.g0 % d.every_k == 0u);
         s_r.gen_sites = a.sites + static_cast<size_t>(run) * a.chunk + a.dg;
+        s_r.effect_scale = 1.0f;
         s_unit = __ldg(&a.unit_local[blockIdx.x]);
     }
     __syncthreads();
@@ -424,7 +425,8 @@ int ga_batch_add(ga_batch *b, ga_run *run)
 {
     if (!b || !run) return GA_EINVAL;
     if (std::find(b->runs.begin(), b->runs.end(), run) != b->runs.end()) return GA_EINVAL;
-    if (!ga::pick(run->cfg.island_size, ga::sw_class(run->surface_words), 0, 8))
+    if (run->cfg.model != GA_MODEL_TRAIT ||
+        !ga::pick(run->cfg.island_size, ga::sw_class(run->surface_words), 0, 8))
         return GA_EUNSUPPORTED;
     if (run->generation + 1 > 0xFFFFFFFFull) return GA_EINVAL;
     // the run's own queued work must be done before the batch stream touches its buffers

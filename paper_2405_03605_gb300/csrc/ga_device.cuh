@@ -80,6 +80,71 @@ __device__ __forceinline__ uint4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2
 }
 
 // ---------------------------------------------------------------------------------------
+// Standard normal deviate from two Philox words (float-fitness model, Sec. 3 "normally
+// distributed amount"): Box-Muller z = sqrt(-2 ln u1) cos(2 pi u2) in IEEE single precision,
+// every operation an explicitly rounded intrinsic (never fused), so the result is a fixed
+// function of the two words:
+//   u1 = (top 24 bits of a, + 1) 2^-24 in (0, 1];
+//   ln u1: u1 = m 2^e, m in [0.5, 1); ln m = 2 atanh(s), s = (m - 1)/(m + 1), series to s^13;
+//   cos(2 pi k 2^-24), k = top 24 bits of b: quadrant k >> 22, angle (k mod 2^22) 2^-22 pi/2,
+//   Taylor series of cos (to a^14) and sin (to a^15).
+// ---------------------------------------------------------------------------------------
+constexpr uint32_t kMutate = 3u;
+
+__device__ __forceinline__ float unit_log_rn(float x)
+{
+    const uint32_t bits = __float_as_uint(x);
+    const int e = static_cast<int>((bits >> 23) & 0xFFu) - 126;
+    const float m = __uint_as_float((bits & 0x007FFFFFu) | 0x3F000000u);
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float t = __fmul_rn(s, s);
+    float p = static_cast<float>(1.0 / 13.0);
+    p = __fadd_rn(__fmul_rn(p, t), static_cast<float>(1.0 / 11.0));
+    p = __fadd_rn(__fmul_rn(p, t), static_cast<float>(1.0 / 9.0));
+    p = __fadd_rn(__fmul_rn(p, t), static_cast<float>(1.0 / 7.0));
+    p = __fadd_rn(__fmul_rn(p, t), static_cast<float>(1.0 / 5.0));
+    p = __fadd_rn(__fmul_rn(p, t), static_cast<float>(1.0 / 3.0));
+    p = __fadd_rn(__fmul_rn(p, t), 1.0f);
+    const float ln_m = __fmul_rn(__fmul_rn(2.0f, s), p);
+    return __fadd_rn(__fmul_rn(static_cast<float>(e), static_cast<float>(0.69314718055994530942)),
+                     ln_m);
+}
+
+__device__ __forceinline__ float turn_cos_rn(uint32_t k)
+{
+    const uint32_t q = (k >> 22) & 3u;
+    const float a = __fmul_rn(__fmul_rn(static_cast<float>(k & 0x3FFFFFu),
+                                        static_cast<float>(1.0 / 4194304.0)),
+                              static_cast<float>(3.14159265358979323846 / 2.0));
+    const float a2 = __fmul_rn(a, a);
+    float c = -static_cast<float>(1.0 / 87178291200.0);
+    c = __fadd_rn(__fmul_rn(c, a2), static_cast<float>(1.0 / 479001600.0));
+    c = __fsub_rn(__fmul_rn(c, a2), static_cast<float>(1.0 / 3628800.0));
+    c = __fadd_rn(__fmul_rn(c, a2), static_cast<float>(1.0 / 40320.0));
+    c = __fsub_rn(__fmul_rn(c, a2), static_cast<float>(1.0 / 720.0));
+    c = __fadd_rn(__fmul_rn(c, a2), static_cast<float>(1.0 / 24.0));
+    c = __fsub_rn(__fmul_rn(c, a2), 0.5f);
+    c = __fadd_rn(__fmul_rn(c, a2), 1.0f);
+    float sn = -static_cast<float>(1.0 / 1307674368000.0);
+    sn = __fadd_rn(__fmul_rn(sn, a2), static_cast<float>(1.0 / 6227020800.0));
+    sn = __fsub_rn(__fmul_rn(sn, a2), static_cast<float>(1.0 / 39916800.0));
+    sn = __fadd_rn(__fmul_rn(sn, a2), static_cast<float>(1.0 / 362880.0));
+    sn = __fsub_rn(__fmul_rn(sn, a2), static_cast<float>(1.0 / 5040.0));
+    sn = __fadd_rn(__fmul_rn(sn, a2), static_cast<float>(1.0 / 120.0));
+    sn = __fsub_rn(__fmul_rn(sn, a2), static_cast<float>(1.0 / 6.0));
+    sn = __fadd_rn(__fmul_rn(sn, a2), 1.0f);
+    sn = __fmul_rn(sn, a);
+    return q == 0u ? c : q == 1u ? -sn : q == 2u ? -c : sn;
+}
+
+__device__ __forceinline__ float normal_rn(uint32_t a, uint32_t b)
+{
+    const float u1 = __fmul_rn(static_cast<float>((a >> 8) + 1u), static_cast<float>(1.0 / 16777216.0));
+    const float r = __fsqrt_rn(__fmul_rn(-2.0f, unit_log_rn(u1)));
+    return __fmul_rn(r, turn_cos_rn(b >> 8));
+}
+
+// ---------------------------------------------------------------------------------------
 // Curation sites in closed form.  -1: the deposit of rank T is not kept.
 //
 // Steady (S = 2^s sites): ranks below S fill sites in order; in epoch t = bitlen(T) - s a

@@ -44,7 +44,7 @@ constexpr uint32_t kMaxGensPerLaunch = 256;
 
 // island_step launch: generations [g0, g0 + n_gens) read from src, write dst; migration (if
 // `migrate`) happens only at g0.
-bool step_supported(uint32_t island_size, uint32_t surface_words);
+bool step_supported(uint32_t island_size, uint32_t surface_words, uint32_t model);
 cudaError_t launch_founder(ga_run *run, void *dst);
 cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t g0,
                                uint32_t n_gens, bool migrate);

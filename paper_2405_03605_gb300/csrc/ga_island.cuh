@@ -38,6 +38,7 @@ struct RunParams {
     uint32_t run_id;
     uint32_t g0, n_gens, migrate;           // migration (if set) happens at g0 only
     const int32_t *__restrict__ gen_sites;  // curation site of generation g0 + i
+    float effect_scale;                     // fitness model: mutation amount scale
 };
 
 // Candidate trait of slot `sel` of this lane's island.  For N <= 32 `sel` may carry extra
@@ -89,9 +90,11 @@ static __device__ __noinline__ int curation_site_of(uint32_t policy, uint32_t lo
 
 // g: the generation; gen_site: its curation site, valid for agents whose counter is g (all
 // agents in synchronous runs) -- any other counter takes the closed form.
-template <int N, int SW, int TS>
+// MODEL 0: int32 trait, +1 / -1; MODEL 1: float fitness, -/+ effect_scale * |normal|.
+template <int N, int SW, int TS, int MODEL>
 __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
                                           const uint4 (&w)[Shape<N>::A], const RunParams &p,
+                                          const RoundKeys &rk, uint32_t island, uint32_t seg_lane,
                                           unsigned mask, uint32_t g, int gen_site)
 {
     constexpr int A = Shape<N>::A, SEG = Shape<N>::SEG, LOGN = Shape<N>::LOGN;
@@ -117,7 +120,10 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
             uint32_t sel = word >> (8 * (i & 3) + 8 - LOGN);
             if constexpr (N > 32) sel &= N - 1u;
             const int t = candidate_trait<N, A, SEG>(mask, trait, sel);
-            if (i == 0 || t > best_trait) {
+            bool better;
+            if constexpr (MODEL == 1) better = __int_as_float(t) > __int_as_float(best_trait);
+            else better = t > best_trait;
+            if (i == 0 || better) {
                 best = sel;
                 best_trait = t;
             }
@@ -149,10 +155,22 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
 #pragma unroll
     for (int ag = 0; ag < A; ++ag) {
         const uint32_t xm = w[ag].z;
-        uint32_t t = child[ag][0];
-        if (xm < p.theta_del) t -= 1u;
-        else if (xm - p.theta_del < p.theta_ben) t += 1u;
-        child[ag][0] = t;
+        if constexpr (MODEL == 1) {
+            const bool del = xm < p.theta_del;
+            const bool ben = !del && xm - p.theta_del < p.theta_ben;
+            if (del || ben) {
+                const uint4 mw = philox_rk(g, island, (seg_lane + 32u * ag) | (kMutate << 16),
+                                           p.run_id, rk);
+                const float amount = __fmul_rn(p.effect_scale, fabsf(normal_rn(mw.x, mw.y)));
+                const float f = __uint_as_float(child[ag][0]);
+                child[ag][0] = __float_as_uint(del ? __fsub_rn(f, amount) : __fadd_rn(f, amount));
+            }
+        } else {
+            uint32_t t = child[ag][0];
+            if (xm < p.theta_del) t -= 1u;
+            else if (xm - p.theta_del < p.theta_ben) t += 1u;
+            child[ag][0] = t;
+        }
 
         const uint32_t c = child[ag][1];
         int site = gen_site;
@@ -175,8 +193,8 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
 // One block's work: `unit` is the block's index within the run (islands
 // [unit * BI, unit * BI + BI)).  N: island size; SW: surface words carried per record (the
 // record is RW words); TS: the tournament size when fixed at compile time (0: read from the
-// run); WARPS: warps per block.
-template <int N, int SW, int TS, int WARPS>
+// run); WARPS: warps per block; MODEL: genome model (0 trait, 1 float fitness).
+template <int N, int SW, int TS, int WARPS, int MODEL = 0>
 __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &rk, uint32_t unit)
 {
     constexpr int A = Shape<N>::A, P = Shape<N>::P, SEG = Shape<N>::SEG;
@@ -293,12 +311,14 @@ __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &
             }
         }
     }
-    reproduce<N, SW, TS>(rec, w, p, mask, p.g0, __ldg(&p.gen_sites[0]));
+    reproduce<N, SW, TS, MODEL>(rec, w, p, rk, island, seg_lane, mask, p.g0,
+                               __ldg(&p.gen_sites[0]));
 
     // generations g0 + 1 .. g0 + n - 1: no migration, the island stays in registers
     for (uint32_t it = 1; it < p.n_gens; ++it) {
         birth_draws<N>(w, p, rk, p.g0 + it, island, seg_lane);
-        reproduce<N, SW, TS>(rec, w, p, mask, p.g0 + it, __ldg(&p.gen_sites[it]));
+        reproduce<N, SW, TS, MODEL>(rec, w, p, rk, island, seg_lane, mask, p.g0 + it,
+                                    __ldg(&p.gen_sites[it]));
     }
 
 #pragma unroll

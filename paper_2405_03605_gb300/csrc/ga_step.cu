@@ -15,10 +15,10 @@ struct StepArgs {
     RoundKeys rk;
 };
 
-template <int N, int SW, int TS>
+template <int N, int SW, int TS, int MODEL = 0>
 __global__ void __launch_bounds__(kStepThreads) island_step_kernel(const StepArgs a)
 {
-    step_block<N, SW, TS, kStepWarps>(a.r, a.rk, blockIdx.x);
+    step_block<N, SW, TS, kStepWarps, MODEL>(a.r, a.rk, blockIdx.x);
 }
 
 // Every record becomes the founder: trait 0, counter 0, surface word w = word 0 of
@@ -77,8 +77,27 @@ StepKernel pick_sw(uint32_t surface_words, uint32_t tsize)
     return nullptr;
 }
 
-StepKernel pick_kernel(uint32_t island_size, uint32_t surface_words, uint32_t tsize)
+// The float-fitness model (16-byte records: fitness, counter, 64-bit surface -- the paper's
+// 128-bit genome of Sec. 3) has kernels for islands of 16, 32 and 64.
+template <int N>
+StepKernel pick_fitness(uint32_t surface_words, uint32_t tsize)
 {
+    if (surface_words > 2) return nullptr;
+    return tsize == 5 ? island_step_kernel<N, 2, 5, 1> : island_step_kernel<N, 2, 0, 1>;
+}
+
+StepKernel pick_kernel(uint32_t island_size, uint32_t surface_words, uint32_t tsize,
+                       uint32_t model)
+{
+    if (model == GA_MODEL_FITNESS) {
+        switch (island_size) {
+        case 16: return pick_fitness<16>(surface_words, tsize);
+        case 32: return pick_fitness<32>(surface_words, tsize);
+        case 64: return pick_fitness<64>(surface_words, tsize);
+        default: return nullptr;
+        }
+    }
+    if (model != GA_MODEL_TRAIT) return nullptr;
     switch (island_size) {
     case 4: return pick_sw<4>(surface_words, tsize);
     case 8: return pick_sw<8>(surface_words, tsize);
@@ -125,12 +144,13 @@ RunParams run_params(const ga_run *run, const void *src, void *dst, uint32_t g0,
     r.n_gens = n_gens;
     r.migrate = migrate ? 1u : 0u;
     r.gen_sites = run->d_sites + (g0 - run->sites_base);
+    r.effect_scale = static_cast<float>(run->cfg.effect_scale);
     return r;
 }
 
-bool step_supported(uint32_t island_size, uint32_t surface_words)
+bool step_supported(uint32_t island_size, uint32_t surface_words, uint32_t model)
 {
-    return pick_kernel(island_size, surface_words, 1) != nullptr;
+    return pick_kernel(island_size, surface_words, 1, model) != nullptr;
 }
 
 cudaError_t launch_founder(ga_run *run, void *dst)
@@ -153,7 +173,8 @@ cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t
                                uint32_t n_gens, bool migrate)
 {
     const StepKernel k =
-        pick_kernel(run->cfg.island_size, run->surface_words, run->cfg.tournament_size);
+        pick_kernel(run->cfg.island_size, run->surface_words, run->cfg.tournament_size,
+                    run->cfg.model);
     if (!k) return cudaErrorInvalidValue;
     StepArgs a;
     a.r = run_params(run, src, dst, g0, n_gens, migrate);

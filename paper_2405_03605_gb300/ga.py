@@ -18,6 +18,7 @@ LIB_PATH = os.environ.get("PAPER_2405_03605_GB300_LIB") or os.path.join(
 
 GA_OK = 0
 STEADY, TILTED, HYBRID = 0, 1, 2
+MODEL_TRAIT, MODEL_FITNESS = 0, 1
 
 EXPORTED = (
     "ga_config_default", "ga_config_check", "ga_record_bytes", "ga_workspace_bytes",
@@ -44,8 +45,8 @@ class GaConfig(C.Structure):
         ("p_ben", C.c_double), ("p_del", C.c_double),
         ("surface_sites", C.c_uint32), ("differentia_bits", C.c_uint32),
         ("curation", C.c_uint32), ("mode", C.c_uint32),
-        ("seed", C.c_uint64), ("run_id", C.c_uint32), ("reserved", C.c_uint32),
-        ("stream", C.c_void_p),
+        ("seed", C.c_uint64), ("run_id", C.c_uint32), ("model", C.c_uint32),
+        ("stream", C.c_void_p), ("effect_scale", C.c_double),
     ]
 
 
@@ -117,7 +118,8 @@ def make_config(shape: RunShape, stream=0):
     cfg = GaConfig()
     load_library().ga_config_default(C.byref(cfg))
     for k in ("rows", "cols", "island_size", "tournament_size", "p_ben", "p_del",
-              "surface_sites", "differentia_bits", "curation", "seed", "run_id"):
+              "surface_sites", "differentia_bits", "curation", "seed", "run_id", "model",
+              "effect_scale"):
         setattr(cfg, k, getattr(shape, k))
     cfg.stream = stream or None
     return cfg

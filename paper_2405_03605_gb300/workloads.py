@@ -14,6 +14,7 @@ import math
 import numpy as np
 
 STEADY, TILTED, HYBRID = 0, 1, 2
+MODEL_TRAIT, MODEL_FITNESS = 0, 1
 
 
 @dataclass(frozen=True)
@@ -31,6 +32,8 @@ class RunShape:
     seed: int = 42
     run_id: int = 0
     generations: int = 1000
+    model: int = MODEL_TRAIT
+    effect_scale: float = 1.0
 
     @property
     def n_islands(self):
@@ -63,6 +66,15 @@ SMALL_TORUS = RunShape(rows=32, cols=32, generations=1000)
 PAPER_ADAPTIVE = RunShape(rows=512, cols=1024, p_ben=0.01, run_id=0, generations=10000)
 PAPER_PURIFYING = RunShape(rows=512, cols=1024, p_ben=0.0, run_id=1, generations=10000)
 PAPER_SAMPLE = 4096
+
+
+# The paper's own treatments (Sec. 3): 128-bit genome whose first 32 bits are a float
+# fitness; purifying-only runs lose fitness by a normally distributed amount at 33% of births,
+# adaptive runs also gain by a normally distributed amount at 0.3% of births; tournament 5.
+PAPER_FITNESS_PURIFYING = RunShape(rows=512, cols=1024, p_ben=0.0, p_del=0.33, run_id=2,
+                                   generations=10000, model=MODEL_FITNESS)
+PAPER_FITNESS_ADAPTIVE = RunShape(rows=512, cols=1024, p_ben=0.003, p_del=0.33, run_id=3,
+                                  generations=10000, model=MODEL_FITNESS)
 
 
 def variant_shapes(island_size=32, migrate_every=1, generations=5000):

@@ -17,7 +17,8 @@ def oracle_for(shape, n_threads=None):
                      p_del=shape.p_del, surface_sites=shape.surface_sites,
                      differentia_bits=shape.differentia_bits, curation=shape.curation,
                      migrate_every=shape.migrate_every, seed=shape.seed, run_id=shape.run_id,
-                     threads=n_threads or threads())
+                     threads=n_threads or threads(), model=shape.model,
+                     effect_scale=shape.effect_scale)
 
 
 def gpu_run(shape):

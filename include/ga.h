@@ -188,7 +188,9 @@ int ga_mrca_bounds_device(ga_run *run, const uint32_t *d_agent_ids, uint32_t n,
  * A run belongs to at most one batch at a time.  Call ga_batch_sync before any per-run call
  * on a member (ga_snapshot, ga_mrca_bounds, ga_step, ga_reset, ga_load, ...); a member whose
  * generation or buffer changed through such calls is picked up by the next ga_batch_step.  Member runs may have different shapes, mutation rates, tournament
- * sizes, curation policies, seeds and migration policies; island sizes 8..64, trait model.
+ * sizes, curation policies, seeds and migration policies.  Members with 65,536 islands or
+ * more, float-fitness runs and island sizes without a batched kernel (4, 128) step with the
+ * single-run kernels on the batch's stream instead of sharing class launches.
  */
 typedef struct ga_batch ga_batch;
 
@@ -197,7 +199,7 @@ typedef struct ga_batch ga_batch;
 int ga_batch_create(void *stream, ga_batch **out);
 
 /* Add a run (synchronises the run's stream and the batch's stream).  GA_EINVAL if it is
-   already a member; GA_EUNSUPPORTED for island sizes without a batched kernel. */
+   already a member. */
 int ga_batch_add(ga_batch *batch, ga_run *run);
 
 /* Remove a member run (synchronises the batch's stream; the run keeps its state). */

@@ -87,6 +87,43 @@ int take_status(ga_run *run)
 
 }  // namespace
 
+namespace ga {
+
+int step_run(ga_run *run, uint32_t n_gens, cudaStream_t stream)
+{
+    if (run->generation + n_gens > 0xFFFFFFFFull) return GA_EINVAL;
+    while (n_gens > 0) {
+        // curation sites of the next chunk of generations, computed on the device once
+        const uint32_t chunk = n_gens < kSiteTableCap ? n_gens : kSiteTableCap;
+        int rc = cuda_rc(launch_site_table(run, static_cast<uint32_t>(run->generation), chunk, stream));
+        if (rc != GA_OK) return rc;
+        run->sites_base = run->generation;
+        uint32_t left = chunk;
+        while (left > 0) {
+            const uint64_t g = run->generation;
+            uint64_t len = left;
+            bool migrate = false;
+            if (run->per_neighbor) {
+                migrate = (g % run->every_k) == 0;
+                const uint64_t next = (g / run->every_k + 1) * run->every_k;
+                if (next - g < len) len = next - g;
+            }
+            if (len > kMaxGensPerLaunch) len = kMaxGensPerLaunch;
+            rc = cuda_rc(launch_island_step(run, run->pop[run->cur], run->pop[run->cur ^ 1],
+                                            static_cast<uint32_t>(g), static_cast<uint32_t>(len),
+                                            migrate, stream));
+            if (rc != GA_OK) return rc;
+            run->cur ^= 1;
+            run->generation += len;
+            left -= static_cast<uint32_t>(len);
+        }
+        n_gens -= chunk;
+    }
+    return GA_OK;
+}
+
+}  // namespace ga
+
 extern "C" {
 
 int ga_config_default(ga_config *cfg)
@@ -207,35 +244,7 @@ int ga_migrate_policy(ga_run *run, uint32_t per_neighbor, uint32_t every_k)
 int ga_step(ga_run *run, uint32_t n_gens)
 {
     if (!run) return GA_EINVAL;
-    if (run->generation + n_gens > 0xFFFFFFFFull) return GA_EINVAL;
-    while (n_gens > 0) {
-        // curation sites of the next chunk of generations, computed on the device once
-        const uint32_t chunk = n_gens < ga::kSiteTableCap ? n_gens : ga::kSiteTableCap;
-        int rc = cuda_rc(ga::launch_site_table(run, static_cast<uint32_t>(run->generation), chunk));
-        if (rc != GA_OK) return rc;
-        run->sites_base = run->generation;
-        uint32_t left = chunk;
-        while (left > 0) {
-            const uint64_t g = run->generation;
-            uint64_t len = left;
-            bool migrate = false;
-            if (run->per_neighbor) {
-                migrate = (g % run->every_k) == 0;
-                const uint64_t next = (g / run->every_k + 1) * run->every_k;
-                if (next - g < len) len = next - g;
-            }
-            if (len > ga::kMaxGensPerLaunch) len = ga::kMaxGensPerLaunch;
-            rc = cuda_rc(ga::launch_island_step(run, run->pop[run->cur], run->pop[run->cur ^ 1],
-                                                static_cast<uint32_t>(g),
-                                                static_cast<uint32_t>(len), migrate));
-            if (rc != GA_OK) return rc;
-            run->cur ^= 1;
-            run->generation += len;
-            left -= static_cast<uint32_t>(len);
-        }
-        n_gens -= chunk;
-    }
-    return GA_OK;
+    return ga::step_run(run, n_gens, run->stream);
 }
 
 int ga_sync(ga_run *run)

@@ -12,6 +12,9 @@
 // replayed; the per-launch generation offset is a kernel parameter, the per-run state lives
 // in device descriptors.
 //
+// Members with 65,536 islands or more (and float-fitness runs) fill the GPU on their own; they
+// step with the single-run kernels on the batch's stream instead of joining a class launch.
+//
 // The autotuner times, on the real member runs (their state is saved and restored around
 // the trials), warps per block for each class and the graph's chunk length, and keeps the
 // fastest; the choice changes no result.
@@ -158,6 +161,17 @@ struct Class {
 uint32_t sw_class(uint32_t surface_words) { return surface_words <= 2 ? 2 : surface_words <= 6 ? 6 : 8; }
 uint32_t ts_class(uint32_t tsize) { return tsize == 5 ? 5 : 0; }
 
+// Members this large fill the GPU on their own: they step with the single-run kernels (their
+// round keys and parameters in the constant bank) instead of joining a class launch; so do
+// members of a model or island size the batched kernels do not cover.
+constexpr uint32_t kSoloIslands = 1u << 16;
+
+bool solo(const ga_run *r)
+{
+    return r->n_islands >= kSoloIslands || r->cfg.model != GA_MODEL_TRAIT ||
+           !pick(r->cfg.island_size, sw_class(r->surface_words), 0, 8);
+}
+
 }  // namespace
 }  // namespace ga
 
@@ -208,6 +222,7 @@ int rebuild(ga_batch *b)
     std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint64_t>, size_t> index;
     for (uint32_t i = 0; i < b->runs.size(); ++i) {
         const ga_run *r = b->runs[i];
+        if (ga::solo(r)) continue;
         const auto key = std::make_tuple(r->cfg.island_size, ga::sw_class(r->surface_words),
                                          ga::ts_class(r->cfg.tournament_size), r->cfg.seed);
         auto it = index.find(key);
@@ -369,6 +384,7 @@ uint64_t chunk_launches(const ga_batch *b, uint32_t chunk)
 
 int step_device(ga_batch *b, uint32_t n_gens)
 {
+    if (b->classes.empty()) return GA_OK;
     int rc = GA_OK;
     uint32_t left = n_gens;
     if (left >= b->chunk) {
@@ -391,9 +407,11 @@ void advance_host(ga_batch *b, uint32_t n_gens)
 {
     for (size_t i = 0; i < b->runs.size(); ++i) {
         ga_run *r = b->runs[i];
-        r->generation += n_gens;
-        r->cur ^= static_cast<int>(n_gens & 1u);
-        r->launches += n_gens;  // one island-step launch per generation covers each run
+        if (!ga::solo(r)) {  // solo members were advanced by their own steps
+            r->generation += n_gens;
+            r->cur ^= static_cast<int>(n_gens & 1u);
+            r->launches += n_gens;  // one island-step launch per generation covers each run
+        }
         b->expect[i] = {r->generation, r->cur};
     }
 }
@@ -425,9 +443,7 @@ int ga_batch_add(ga_batch *b, ga_run *run)
 {
     if (!b || !run) return GA_EINVAL;
     if (std::find(b->runs.begin(), b->runs.end(), run) != b->runs.end()) return GA_EINVAL;
-    if (run->cfg.model != GA_MODEL_TRAIT ||
-        !ga::pick(run->cfg.island_size, ga::sw_class(run->surface_words), 0, 8))
-        return GA_EUNSUPPORTED;
+
     if (run->generation + 1 > 0xFFFFFFFFull) return GA_EINVAL;
     // the run's own queued work must be done before the batch stream touches its buffers
     if (cudaStreamSynchronize(run->stream) != cudaSuccess) return GA_ECUDA;
@@ -467,6 +483,11 @@ int ga_batch_step(ga_batch *b, uint32_t n_gens)
             if (cudaStreamSynchronize(r->stream) != cudaSuccess) return GA_ECUDA;
         const int rc = rebuild(b);
         if (rc != GA_OK) return rc;
+    }
+    for (ga_run *r : b->runs) {
+        if (!ga::solo(r)) continue;
+        const int rs = ga::step_run(r, n_gens, b->stream);
+        if (rs != GA_OK) return rs;
     }
     const int rc = step_device(b, n_gens);
     if (rc != GA_OK) return rc;

@@ -47,9 +47,12 @@ constexpr uint32_t kMaxGensPerLaunch = 256;
 bool step_supported(uint32_t island_size, uint32_t surface_words, uint32_t model);
 cudaError_t launch_founder(ga_run *run, void *dst);
 cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t g0,
-                               uint32_t n_gens, bool migrate);
+                               uint32_t n_gens, bool migrate, cudaStream_t stream);
 // Fill the site table with the curation sites of generations [g0, g0 + count).
-cudaError_t launch_site_table(ga_run *run, uint32_t g0, uint32_t count);
+cudaError_t launch_site_table(ga_run *run, uint32_t g0, uint32_t count, cudaStream_t stream);
+// Advance one run by n_gens generations with the single-run kernels on `stream` (the body of
+// ga_step; the batch uses it for members that fill the GPU on their own).
+int step_run(ga_run *run, uint32_t n_gens, cudaStream_t stream);
 cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t *d_lo,
                         uint32_t *d_hi, void *scratch);
 size_t mrca_scratch_bytes(const ga_run *run, uint32_t n);

@@ -170,7 +170,7 @@ cudaError_t launch_founder(ga_run *run, void *dst)
 }
 
 cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t g0,
-                               uint32_t n_gens, bool migrate)
+                               uint32_t n_gens, bool migrate, cudaStream_t stream)
 {
     const StepKernel k =
         pick_kernel(run->cfg.island_size, run->surface_words, run->cfg.tournament_size,
@@ -183,15 +183,15 @@ cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t
     const uint32_t N = run->cfg.island_size;
     const uint32_t islands_per_block = kStepWarps * (N >= 32 ? 1u : 32u / N);
     const uint32_t blocks = (run->n_islands + islands_per_block - 1) / islands_per_block;
-    k<<<blocks, kStepThreads, 0, run->stream>>>(a);
+    k<<<blocks, kStepThreads, 0, stream>>>(a);
     run->launches += 1;
     return cudaGetLastError();
 }
 
-cudaError_t launch_site_table(ga_run *run, uint32_t g0, uint32_t count)
+cudaError_t launch_site_table(ga_run *run, uint32_t g0, uint32_t count, cudaStream_t stream)
 {
     const cudaError_t e = launch_curation_sites(run->cfg.curation, run->cfg.surface_sites, g0,
-                                                count, run->d_sites, run->stream);
+                                                count, run->d_sites, stream);
     run->launches += 1;
     return e;
 }

@@ -90,3 +90,24 @@ def test_autotune_changes_no_result():
         alone.sync()
         assert np.array_equal(r.snapshot(), alone.snapshot())
     batch.close()
+
+
+def test_large_member_steps_solo_bit_identical():
+    from paper_2405_03605_gb300 import ga
+    shapes = [RunShape(rows=256, cols=256, island_size=16, seed=3, run_id=40),  # 65,536 islands
+              RunShape(rows=6, cols=5, island_size=32, seed=3, run_id=41)]
+    runs = [gpu_run(s) for s in shapes]
+    batch = ga.Batch(runs)
+    batch.step(9)
+    batch.step(4)
+    batch.sync()
+    for s, r in zip(shapes, runs):
+        alone = gpu_run(s)
+        alone.step(13)
+        alone.sync()
+        assert r.generation == 13
+        assert np.array_equal(r.snapshot(), alone.snapshot())
+    o = oracle_for(shapes[1])
+    o.step(13)
+    assert_same(runs[1].snapshot(), o.snapshot(), 32)
+    batch.close()

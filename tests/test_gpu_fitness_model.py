@@ -38,8 +38,21 @@ def test_fitness_model_rejected_where_unsupported():
     from paper_2405_03605_gb300 import ga
     assert ga.config_check(RunShape(rows=2, cols=2, island_size=8, model=MODEL_FITNESS)) == -6
     assert ga.config_check(RunShape(rows=2, cols=2, model=MODEL_FITNESS, effect_scale=0.0)) == -1
-    run = gpu_run(RunShape(rows=2, cols=2, model=MODEL_FITNESS))
-    batch = ga.Batch()
-    with pytest.raises(ga.GaError):
-        batch.add(run)
+
+
+def test_fitness_runs_step_solo_inside_a_batch():
+    from paper_2405_03605_gb300 import ga
+    a = RunShape(rows=4, cols=6, model=MODEL_FITNESS, p_ben=0.003, p_del=0.33, seed=5, run_id=1)
+    b = RunShape(rows=5, cols=3, seed=5, run_id=2)
+    runs = [gpu_run(a), gpu_run(b)]
+    batch = ga.Batch(runs)
+    batch.step(40)
+    batch.step(3)
+    batch.sync()
+    for s, r in zip((a, b), runs):
+        o = oracle_for(s)
+        o.step(43)
+        assert r.generation == 43
+        assert_same(r.snapshot(), o.snapshot(), s.island_size)
     batch.close()
+

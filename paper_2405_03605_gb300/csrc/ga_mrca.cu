@@ -121,17 +121,18 @@ __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_wo
 }
 
 // One thread per pair: block (x, y) covers row i = y and columns j = i + 1 + 256 x + t.  The
-// first set bit of packed[i] ^ packed[j] gives the first mismatching rank index i*.
+// first set bit of packed[i] ^ packed[j] gives the first mismatching rank index i*.  WIDE:
+// the rank-ordered strings need more than 64 bits (otherwise one 64-bit word decides).
+template <bool WIDE>
 __global__ void __launch_bounds__(kPairThreads)
 pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__restrict__ ranks_g,
-            const uint32_t *__restrict__ meta, uint32_t bits, uint32_t K, uint32_t T,
+            const uint32_t *__restrict__ meta, uint32_t log2_bits, uint32_t K, uint32_t T,
             uint32_t *__restrict__ lo, uint32_t *__restrict__ hi)
 {
     __shared__ uint32_t ranks[256];
     __shared__ uint32_t mine[kPackWords];
     const uint32_t m = meta[0];
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ranks[i] = ranks_g[i];
-    const uint32_t pw = (m * bits + 31u) >> 5;
     for (uint32_t row = blockIdx.y; row < n; row += gridDim.y) {
         const uint32_t j0 = row + 1u + blockIdx.x * kPairThreads;
         if (j0 >= n) continue;  // uniform across the block
@@ -139,26 +140,29 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
         __syncthreads();
         const uint32_t j = j0 + threadIdx.x;
         if (j < n) {
-            const uint4 *pj = reinterpret_cast<const uint4 *>(packed + static_cast<size_t>(j) * kPackWords);
-            const uint4 b0 = __ldg(&pj[0]);
-            uint32_t x[kPackWords];
-            x[0] = b0.x ^ mine[0]; x[1] = b0.y ^ mine[1]; x[2] = b0.z ^ mine[2]; x[3] = b0.w ^ mine[3];
-            if (pw > 4u) {
-                const uint4 b1 = __ldg(&pj[1]);
-                x[4] = b1.x ^ mine[4]; x[5] = b1.y ^ mine[5]; x[6] = b1.z ^ mine[6]; x[7] = b1.w ^ mine[7];
-            } else {
-                x[4] = x[5] = x[6] = x[7] = 0u;
-            }
+            const uint32_t *pj = packed + static_cast<size_t>(j) * kPackWords;
             uint32_t first_bit = 0xFFFFFFFFu;
+            if constexpr (!WIDE) {
+                const uint2 b0 = __ldg(reinterpret_cast<const uint2 *>(pj));
+                const unsigned long long x =
+                    (static_cast<unsigned long long>(b0.y ^ mine[1]) << 32) | (b0.x ^ mine[0]);
+                if (x != 0ull) first_bit = static_cast<uint32_t>(__ffsll(static_cast<long long>(x)) - 1);
+            } else {
+                const uint4 b0 = __ldg(reinterpret_cast<const uint4 *>(pj));
+                const uint4 b1 = __ldg(reinterpret_cast<const uint4 *>(pj) + 1);
+                const uint32_t x[kPackWords] = {b0.x ^ mine[0], b0.y ^ mine[1], b0.z ^ mine[2],
+                                                b0.w ^ mine[3], b1.x ^ mine[4], b1.y ^ mine[5],
+                                                b1.z ^ mine[6], b1.w ^ mine[7]};
 #pragma unroll
-            for (int w = kPackWords - 1; w >= 0; --w)
-                if (x[w] != 0u) first_bit = 32u * w + (__ffs(x[w]) - 1u);
+                for (int w = kPackWords - 1; w >= 0; --w)
+                    if (x[w] != 0u) first_bit = 32u * w + (__ffs(x[w]) - 1u);
+            }
             uint32_t l, h;
             if (first_bit == 0xFFFFFFFFu) {
                 h = T;
                 l = m >= K ? ranks[m - K] + 1u : 0u;
             } else {
-                const uint32_t istar = first_bit / bits;  // 0-based index of the first mismatch
+                const uint32_t istar = first_bit >> log2_bits;  // first mismatch, 0-based
                 h = ranks[istar];
                 l = istar >= K ? ranks[istar - K] + 1u : 0u;
             }
@@ -173,14 +177,21 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
 // pack + pair launches shared by the allocating and the fixed-scratch entry points
 void launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, uint32_t n_agents,
                            const uint32_t *d_ids, uint32_t n, const uint32_t *order,
-                           const uint32_t *ranks, const uint32_t *meta, uint32_t bits, uint32_t K,
-                           uint32_t T, uint32_t *packed, uint32_t *d_lo, uint32_t *d_hi,
-                           int *status, cudaStream_t stream)
+                           const uint32_t *ranks, const uint32_t *meta, uint32_t sites,
+                           uint32_t bits, uint32_t K, uint32_t T, uint32_t *packed,
+                           uint32_t *d_lo, uint32_t *d_hi, int *status, cudaStream_t stream)
 {
     pack_kernel<<<(n + 7u) / 8u, 256, 0, stream>>>(pop, record_words, n_agents, d_ids, n, order,
                                                    meta, bits, T, packed, status);
     const dim3 grid((n + kPairThreads - 1) / kPairThreads, n < 65535u ? n : 65535u);
-    pair_kernel<<<grid, kPairThreads, 0, stream>>>(packed, n, ranks, meta, bits, K, T, d_lo, d_hi);
+    const uint32_t log2_bits = bits == 1u ? 0u : bits == 2u ? 1u : bits == 4u ? 2u : 3u;
+    // sites * bits <= 64: every rank-ordered string fits in its first 64 bits
+    if (sites * bits <= 64u)
+        pair_kernel<false><<<grid, kPairThreads, 0, stream>>>(packed, n, ranks, meta, log2_bits,
+                                                               K, T, d_lo, d_hi);
+    else
+        pair_kernel<true><<<grid, kPairThreads, 0, stream>>>(packed, n, ranks, meta, log2_bits, K,
+                                                              T, d_lo, d_hi);
 }
 
 uint32_t margin(uint32_t bits)
@@ -218,7 +229,7 @@ cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t
     run->launches += 1;
     launch_pack_and_pairs(reinterpret_cast<const uint32_t *>(run->pop[run->cur]),
                           run->record_bytes / 4u, run->n_agents, d_ids, n, l.order, l.ranks,
-                          l.meta, b, margin(b), T, l.packed, d_lo, d_hi, run->d_status,
+                          l.meta, S, b, margin(b), T, l.packed, d_lo, d_hi, run->d_status,
                           run->stream);
     run->launches += 2;
     return cudaGetLastError();
@@ -313,7 +324,7 @@ extern "C" int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_byt
     }
     order_kernel<<<1, 256, 0, st>>>(l.holder, l.order, l.ranks, l.meta, S);
     launch_pack_and_pairs(static_cast<const uint32_t *>(d_records), record_bytes / 4u, n_agents,
-                          d_agent_ids, n, l.order, l.ranks, l.meta, b, margin(b), generation,
+                          d_agent_ids, n, l.order, l.ranks, l.meta, S, b, margin(b), generation,
                           l.packed, d_lo, d_hi, status, st);
     if (cudaGetLastError() != cudaSuccess) return GA_ECUDA;
     int device_status = GA_OK;

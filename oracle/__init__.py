@@ -21,6 +21,7 @@ from .oracle import (  # noqa: F401
     site_ranks,
     mrca_margin,
     mrca_bounds,
+    mrca_bounds_mixed,
     record_bytes,
     openmp_enabled,
 )

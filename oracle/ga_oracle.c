@@ -691,6 +691,96 @@ int orc_mrca_bounds(const void *records, uint32_t record_bytes, const uint32_t *
     return 0;
 }
 
+/*
+ * Pairwise MRCA bounds when the sampled agents' counters may differ (asynchronous runs: an
+ * immigrant carries the counter of the island it was born in).  A rank r is only ever
+ * deposited at site(r), so agents a and b (counters Ta, Tb) share rank r exactly when their
+ * site -> rank tables at Ta and Tb hold r at the same site.  Over those common ranks, in rank
+ * order c_1 < ... < c_m:
+ *   first mismatch at c_{i*}: hi = c_{i*}, lo = c_{i*-K} + 1 (0 when i* <= K);
+ *   no mismatch: hi = min(Ta, Tb), lo = c_{m-K+1} + 1 (0 when m < K).
+ * With Ta = Tb this is orc_mrca_bounds.  Returns 0, or -2 when out of memory.
+ */
+typedef struct {
+    uint64_t T;
+    int64_t *table;
+} rank_table;
+
+static const int64_t *table_for(rank_table *cache, uint32_t *n_cached, uint32_t policy, uint32_t S,
+                                uint64_t T)
+{
+    for (uint32_t i = 0; i < *n_cached; ++i)
+        if (cache[i].T == T) return cache[i].table;
+    int64_t *t = (int64_t *)malloc(S * sizeof(int64_t));
+    if (!t) return NULL;
+    orc_site_ranks(policy, S, T, t);
+    cache[*n_cached].T = T;
+    cache[*n_cached].table = t;
+    *n_cached += 1;
+    return t;
+}
+
+int orc_mrca_bounds_mixed(const void *records, uint32_t record_bytes, const uint32_t *ids,
+                          uint32_t n, uint32_t policy, uint32_t S, uint32_t b, uint32_t *lo,
+                          uint32_t *hi)
+{
+    const uint8_t *base = (const uint8_t *)records;
+    rank_table *cache = (rank_table *)calloc(n ? n : 1, sizeof(rank_table));
+    const int64_t **tab = (const int64_t **)calloc(n ? n : 1, sizeof(int64_t *));
+    uint32_t *cnt = (uint32_t *)calloc(n ? n : 1, sizeof(uint32_t));
+    int64_t *crank = (int64_t *)malloc(S * sizeof(int64_t));
+    uint32_t *csite = (uint32_t *)malloc(S * sizeof(uint32_t));
+    uint32_t n_cached = 0;
+    int rc = 0;
+    if (!cache || !tab || !cnt || !crank || !csite) rc = -2;
+    for (uint32_t i = 0; i < n && rc == 0; ++i) {
+        memcpy(&cnt[i], base + (size_t)ids[i] * record_bytes + 4, 4);
+        tab[i] = table_for(cache, &n_cached, policy, S, cnt[i]);
+        if (!tab[i]) rc = -2;
+    }
+    const uint32_t K = orc_mrca_margin(b);
+    uint64_t p = 0;
+    for (uint32_t i = 0; i < n && rc == 0; ++i) {
+        const uint8_t *ra = base + (size_t)ids[i] * record_bytes;
+        for (uint32_t j = i + 1; j < n; ++j, ++p) {
+            const uint8_t *rb = base + (size_t)ids[j] * record_bytes;
+            /* common ranks, sorted ascending (insertion sort: S is small) */
+            uint32_t m = 0;
+            for (uint32_t k = 0; k < S; ++k) {
+                if (tab[i][k] < 0 || tab[i][k] != tab[j][k]) continue;
+                uint32_t q = m++;
+                while (q > 0 && crank[q - 1] > tab[i][k]) {
+                    crank[q] = crank[q - 1];
+                    csite[q] = csite[q - 1];
+                    --q;
+                }
+                crank[q] = tab[i][k];
+                csite[q] = k;
+            }
+            uint32_t first = 0;
+            for (uint32_t q = 0; q < m; ++q)
+                if (differentia(ra, csite[q], b) != differentia(rb, csite[q], b)) {
+                    first = q + 1;
+                    break;
+                }
+            if (first) {
+                hi[p] = (uint32_t)crank[first - 1];
+                lo[p] = first > K ? (uint32_t)crank[first - 1 - K] + 1u : 0u;
+            } else {
+                hi[p] = cnt[i] < cnt[j] ? cnt[i] : cnt[j];
+                lo[p] = m >= K ? (uint32_t)crank[m - K] + 1u : 0u;
+            }
+        }
+    }
+    for (uint32_t i = 0; i < n_cached; ++i) free(cache[i].table);
+    free(cache);
+    free(tab);
+    free(cnt);
+    free(crank);
+    free(csite);
+    return rc;
+}
+
 /* Oracle-side state accessors for tests. */
 const int32_t *orc_traits(const orc_state *st) { return st->trait; }
 const uint32_t *orc_counters(const orc_state *st) { return st->counter; }

@@ -62,6 +62,9 @@ def _load():
     lib.orc_unit_log.restype = C.c_float
     lib.orc_turn_cos.argtypes = [C.c_uint32]
     lib.orc_turn_cos.restype = C.c_float
+    lib.orc_mrca_bounds_mixed.argtypes = [C.c_void_p, C.c_uint32, u32p, C.c_uint32, C.c_uint32,
+                                          C.c_uint32, C.c_uint32, u32p, u32p]
+    lib.orc_mrca_bounds_mixed.restype = C.c_int
     lib.orc_openmp_enabled.argtypes = []
     lib.orc_openmp_enabled.restype = C.c_int
     _lib = lib
@@ -154,6 +157,24 @@ def unit_log(x):
 def turn_cos(k):
     """cos(2 pi k / 2^24) for a 24-bit k."""
     return float(_load().orc_turn_cos(k))
+
+
+def mrca_bounds_mixed(records, ids, policy, S, b):
+    """Pairwise (lo, hi) bounds from each agent's own counter (counters may differ)."""
+    lib = _load()
+    records = np.ascontiguousarray(records, dtype=np.uint8)
+    rb = record_bytes(S, b)
+    ids_a, idp = _u32(ids)
+    n = len(ids_a)
+    npairs = n * (n - 1) // 2
+    lo = np.zeros(npairs, np.uint32)
+    hi = np.zeros(npairs, np.uint32)
+    rc = lib.orc_mrca_bounds_mixed(records.ctypes.data, rb, idp, n, policy, S, b,
+                                   lo.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                   hi.ctypes.data_as(C.POINTER(C.c_uint32)))
+    if rc != 0:
+        raise ValueError(f"oracle mrca_bounds_mixed failed ({rc})")
+    return lo, hi
 
 
 def openmp_enabled():

@@ -139,3 +139,62 @@ def test_ga_pedigree_bracket():
             misses += D < lo[p]
             p += 1
     assert misses / p < 0.10
+
+
+def test_mixed_equals_uniform_when_counters_equal():
+    S, b, T = 64, 1, 700
+    rng = np.random.default_rng(8)
+    surfs = [[int(x) for x in rng.integers(0, 2 ** 32, 2)] for _ in range(12)]
+    rec = _records_from_surfaces(surfs, S, b, T)
+    ids = list(range(12))
+    lo, hi = oracle.mrca_bounds(rec, ids, STEADY, S, b, T)
+    lo2, hi2 = oracle.mrca_bounds_mixed(rec, ids, STEADY, S, b)
+    assert np.array_equal(lo, lo2) and np.array_equal(hi, hi2)
+
+
+def _fork_trial_mixed(policy, S, b, D, Ta, Tb, sites, rng):
+    """Lineages split at D, then run to different counters Ta and Tb (as after asynchronous
+    migration); returns the mixed-counter bounds of the two end agents."""
+    words = (S * b + 31) // 32
+    mask = (1 << b) - 1
+    base = [int(x) for x in rng.integers(0, 2 ** 32, words)]
+
+    def dep(surf, t):
+        site = sites[t]
+        if site >= 0:
+            pos = site * b
+            w, sh = pos // 32, pos % 32
+            surf[w] = (surf[w] & ~(mask << sh)) | (int(rng.integers(0, mask + 1)) << sh)
+
+    for t in range(D):
+        dep(base, t)
+    a, c = list(base), list(base)
+    for t in range(D, Ta):
+        dep(a, t)
+    for t in range(D, Tb):
+        dep(c, t)
+    rb = oracle.record_bytes(S, b)
+    rec = np.zeros((2, rb), np.uint8)
+    for i, (s, T) in enumerate(((a, Ta), (c, Tb))):
+        rec[i, 4:8] = np.array([T], np.uint32).view(np.uint8)
+        rec[i, 8:8 + 4 * words] = np.array(s, np.uint32).view(np.uint8)
+    lo, hi = oracle.mrca_bounds_mixed(rec, [0, 1], policy, S, b)
+    return int(lo[0]), int(hi[0])
+
+
+@pytest.mark.parametrize("policy,S,b", [(STEADY, 64, 1), (TILTED, 32, 8), (HYBRID, 64, 1)])
+def test_mixed_counter_bracket(policy, S, b):
+    rng = np.random.default_rng(S * 7 + b)
+    T_max = 1200
+    sites = [oracle.site(policy, S, t) for t in range(T_max)]
+    trials, misses = 1200, 0
+    for _ in range(trials):
+        Ta = int(rng.integers(600, T_max))
+        Tb = int(np.clip(Ta + rng.integers(-40, 41), 1, T_max - 1))
+        D = int(rng.integers(0, min(Ta, Tb) + 1))
+        lo, hi = _fork_trial_mixed(policy, S, b, D, Ta, Tb, sites, rng)
+        assert lo <= hi <= min(Ta, Tb)
+        assert D <= hi, (D, lo, hi, Ta, Tb)
+        misses += D < lo
+    p_miss = 2.0 ** (-b * oracle.mrca_margin(b))
+    assert misses / trials <= p_miss + 4 * np.sqrt(p_miss / trials) + 1e-9

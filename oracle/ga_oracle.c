@@ -291,6 +291,21 @@ typedef struct {
     int32_t *trait2;
     uint32_t *counter2;
     uint32_t *surface2;
+    /* asynchronous mode: per island and direction, the outgoing mailbox (sequence number and
+       one agent) and the last sequence number taken from that neighbour; allocated on first
+       use, all zero = nothing posted, nothing taken */
+    uint32_t *mail_seq;
+    int32_t *mail_trait;
+    uint32_t *mail_counter;
+    uint32_t *mail_surface;
+    uint32_t *seen;
+    /* lineage tracking (tests only; off unless orc_track_lineage was called): every agent
+       carries the id of the birth that made it, g * n_agents + slot (-1: founder); event_parent
+       maps a birth to its parent's birth, event_depth to the child's counter */
+    int64_t *tag, *tag2, *mail_tag;
+    int64_t *event_parent;
+    uint32_t *event_depth;
+    uint64_t event_cap;   /* generations covered by the event arrays */
 } orc_state;
 
 /* probability -> 32-bit threshold, once, in IEEE double: theta = min(2^32-1, floor(p 2^32)) */
@@ -336,6 +351,16 @@ void orc_destroy(orc_state *st)
     free(st->trait2);
     free(st->counter2);
     free(st->surface2);
+    free(st->mail_seq);
+    free(st->mail_trait);
+    free(st->mail_counter);
+    free(st->mail_surface);
+    free(st->seen);
+    free(st->tag);
+    free(st->tag2);
+    free(st->mail_tag);
+    free(st->event_parent);
+    free(st->event_depth);
     free(st);
 }
 
@@ -410,6 +435,34 @@ static void copy_agent(orc_state *st, int32_t *t_dst, uint32_t *c_dst, uint32_t 
            st->words * sizeof(uint32_t));
 }
 
+/* Lineage tags follow genomes: a copy keeps the tag, a birth gets a new one. */
+static int tracking(const orc_state *st) { return st->tag != NULL; }
+
+static void record_birth(orc_state *st, uint32_t g, uint32_t child, uint32_t parent)
+{
+    const uint64_t id = (uint64_t)g * st->n_agents + child;
+    st->event_parent[id] = st->tag[parent];
+    st->event_depth[id] = st->counter2[child] + 1u; /* the child's counter after the birth */
+    st->tag2[child] = (int64_t)id;
+}
+
+/* Make room for birth records of generations below `gen_end`. */
+static int reserve_events(orc_state *st, uint64_t gen_end)
+{
+    if (!tracking(st) || gen_end <= st->event_cap) return 0;
+    uint64_t cap = st->event_cap ? st->event_cap : 64;
+    while (cap < gen_end) cap *= 2;
+    const size_t n = (size_t)(cap * st->n_agents);
+    int64_t *p = (int64_t *)realloc(st->event_parent, n * sizeof(int64_t));
+    if (!p) return -2;
+    st->event_parent = p;
+    uint32_t *d = (uint32_t *)realloc(st->event_depth, n * sizeof(uint32_t));
+    if (!d) return -2;
+    st->event_depth = d;
+    st->event_cap = cap;
+    return 0;
+}
+
 /*
  * Migration of generation g (Sec. 2: handled first; each island receives genomes from its
  * four cardinal neighbours, which replace randomly chosen members).  Reading used here:
@@ -433,6 +486,7 @@ void orc_migrate(orc_state *st, uint32_t *src_ids)
     memcpy(st->trait2, st->trait, st->n_agents * sizeof(int32_t));
     memcpy(st->counter2, st->counter, st->n_agents * sizeof(uint32_t));
     memcpy(st->surface2, st->surface, (size_t)st->n_agents * st->words * sizeof(uint32_t));
+    if (tracking(st)) memcpy(st->tag2, st->tag, st->n_agents * sizeof(int64_t));
     if (src_ids)
         for (uint32_t a = 0; a < st->n_agents; ++a) src_ids[a] = a;
 
@@ -453,6 +507,7 @@ void orc_migrate(orc_state *st, uint32_t *src_ids)
             uint32_t src = neighbour(c, isl, (int)d) * N + e;
             copy_agent(st, st->trait, st->counter, st->surface, dst, st->trait2, st->counter2,
                        st->surface2, src);
+            if (tracking(st)) st->tag[dst] = st->tag2[src];
             if (src_ids) src_ids[dst] = src;
         }
     }
@@ -472,72 +527,77 @@ void orc_migrate(orc_state *st, uint32_t *src_ids)
  *     low b bits of B3 overwrite bits [site*b, site*b + b) of the surface; then c += 1.
  * parent_slots (optional, n_agents) receives the winning slot index of every child.
  */
-void orc_reproduce(orc_state *st, uint32_t *parent_slots)
+static void reproduce_island(orc_state *st, uint32_t isl, uint32_t g, uint32_t *parent_slots)
 {
     const orc_config *c = &st->cfg;
     const uint32_t N = c->island_size, n = c->tournament_size, b = c->differentia_bits;
-    const uint32_t g = (uint32_t)st->gen;
     const uint32_t words = st->words;
-
-#pragma omp parallel for schedule(static) num_threads(worker_threads(st))
-    for (int64_t isl64 = 0; isl64 < (int64_t)st->n_islands; ++isl64) {
-        uint32_t isl = (uint32_t)isl64;
-        const uint32_t base = isl * N;
-        for (uint32_t j = 0; j < N; ++j) {
-            uint32_t w[4];
-            draw(c->seed, g, isl, j, ORC_PURPOSE_BIRTH, c->run_id, w);
-            /* tournament */
-            uint32_t best = 0;
-            for (uint32_t i = 0; i < n; ++i) {
-                uint32_t word = i < 4 ? w[0] : w[1];
-                uint32_t byte = (word >> (8 * (i % 4))) & 0xFFu;
-                uint32_t idx = (byte * N) >> 8;
-                int better;
-                if (c->model == ORC_MODEL_FITNESS) {
-                    float fi, fb;
-                    memcpy(&fi, &st->trait[base + idx], 4);
-                    memcpy(&fb, &st->trait[base + best], 4);
-                    better = fi > fb;
-                } else {
-                    better = st->trait[base + idx] > st->trait[base + best];
-                }
-                if (i == 0 || better) best = idx;
-            }
-            if (parent_slots) parent_slots[base + j] = best;
-            /* copy */
-            uint32_t child = base + j, parent = base + best;
-            copy_agent(st, st->trait2, st->counter2, st->surface2, child, st->trait,
-                       st->counter, st->surface, parent);
-            /* mutate */
-            uint32_t x = w[2];
-            int del = x < st->theta_del;
-            int ben = !del && x - st->theta_del < st->theta_ben;
+    const uint32_t base = isl * N;
+    for (uint32_t j = 0; j < N; ++j) {
+        uint32_t w[4];
+        draw(c->seed, g, isl, j, ORC_PURPOSE_BIRTH, c->run_id, w);
+        /* tournament */
+        uint32_t best = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            uint32_t word = i < 4 ? w[0] : w[1];
+            uint32_t byte = (word >> (8 * (i % 4))) & 0xFFu;
+            uint32_t idx = (byte * N) >> 8;
+            int better;
             if (c->model == ORC_MODEL_FITNESS) {
-                if (del || ben) {
-                    uint32_t mw[4];
-                    draw(c->seed, g, isl, j, ORC_PURPOSE_MUTATE, c->run_id, mw);
-                    const float amount = (float)c->effect_scale * fabsf(orc_normal(mw[0], mw[1]));
-                    float f;
-                    memcpy(&f, &st->trait2[child], 4);
-                    f = del ? f - amount : f + amount;
-                    memcpy(&st->trait2[child], &f, 4);
-                }
-            } else if (del) {
-                st->trait2[child] = (int32_t)((uint32_t)st->trait2[child] - 1u);
-            } else if (ben) {
-                st->trait2[child] = (int32_t)((uint32_t)st->trait2[child] + 1u);
+                float fi, fb;
+                memcpy(&fi, &st->trait[base + idx], 4);
+                memcpy(&fb, &st->trait[base + best], 4);
+                better = fi > fb;
+            } else {
+                better = st->trait[base + idx] > st->trait[base + best];
             }
-            /* hstrat deposit for the elapsed generation */
-            int64_t site = orc_site(c->curation, c->surface_sites, st->counter2[child]);
-            if (site >= 0) {
-                uint32_t pos = (uint32_t)site * b;
-                uint32_t *sw = &st->surface2[(size_t)child * words + pos / 32];
-                uint32_t mask = (b == 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)) << (pos % 32);
-                *sw = (*sw & ~mask) | ((w[3] << (pos % 32)) & mask);
-            }
-            st->counter2[child] += 1u;
+            if (i == 0 || better) best = idx;
         }
+        if (parent_slots) parent_slots[base + j] = best;
+        /* copy */
+        uint32_t child = base + j, parent = base + best;
+        copy_agent(st, st->trait2, st->counter2, st->surface2, child, st->trait,
+                   st->counter, st->surface, parent);
+        if (tracking(st)) record_birth(st, g, child, parent);
+        /* mutate */
+        uint32_t x = w[2];
+        int del = x < st->theta_del;
+        int ben = !del && x - st->theta_del < st->theta_ben;
+        if (c->model == ORC_MODEL_FITNESS) {
+            if (del || ben) {
+                uint32_t mw[4];
+                draw(c->seed, g, isl, j, ORC_PURPOSE_MUTATE, c->run_id, mw);
+                const float amount = (float)c->effect_scale * fabsf(orc_normal(mw[0], mw[1]));
+                float f;
+                memcpy(&f, &st->trait2[child], 4);
+                f = del ? f - amount : f + amount;
+                memcpy(&st->trait2[child], &f, 4);
+            }
+        } else if (del) {
+            st->trait2[child] = (int32_t)((uint32_t)st->trait2[child] - 1u);
+        } else if (ben) {
+            st->trait2[child] = (int32_t)((uint32_t)st->trait2[child] + 1u);
+        }
+        /* hstrat deposit for the elapsed generation */
+        int64_t site = orc_site(c->curation, c->surface_sites, st->counter2[child]);
+        if (site >= 0) {
+            uint32_t pos = (uint32_t)site * b;
+            uint32_t *sw = &st->surface2[(size_t)child * words + pos / 32];
+            uint32_t mask = (b == 32 ? 0xFFFFFFFFu : ((1u << b) - 1u)) << (pos % 32);
+            *sw = (*sw & ~mask) | ((w[3] << (pos % 32)) & mask);
+        }
+        st->counter2[child] += 1u;
     }
+}
+
+/* One generation of every island (each reads only its own members), then g += 1. */
+void orc_reproduce(orc_state *st, uint32_t *parent_slots)
+{
+    const uint32_t g = (uint32_t)st->gen;
+    if (reserve_events(st, st->gen + 1) != 0) abort();
+#pragma omp parallel for schedule(static) num_threads(worker_threads(st))
+    for (int64_t isl64 = 0; isl64 < (int64_t)st->n_islands; ++isl64)
+        reproduce_island(st, (uint32_t)isl64, g, parent_slots);
     /* the next population replaces the current one */
     int32_t *tt = st->trait;
     st->trait = st->trait2;
@@ -548,6 +608,9 @@ void orc_reproduce(orc_state *st, uint32_t *parent_slots)
     uint32_t *ss = st->surface;
     st->surface = st->surface2;
     st->surface2 = ss;
+    int64_t *gg = st->tag;
+    st->tag = st->tag2;
+    st->tag2 = gg;
     st->gen += 1;
 }
 
@@ -559,6 +622,121 @@ void orc_step(orc_state *st, uint32_t n_gens)
         if (k != 0 && st->gen % k == 0) orc_migrate(st, NULL);
         orc_reproduce(st, NULL);
     }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Asynchronous migration (Sec. 2: the wafer-scale loop posts and collects migrants       */
+/* without waiting), on the sequential schedule: within a window of generations the       */
+/* islands run one after another in index order, each through all of the window.          */
+/* ------------------------------------------------------------------------------------ */
+
+static int async_alloc(orc_state *st)
+{
+    if (st->mail_seq) return 0;
+    const size_t boxes = (size_t)st->n_islands * 4;
+    st->mail_seq = (uint32_t *)calloc(boxes, sizeof(uint32_t));
+    st->mail_trait = (int32_t *)calloc(boxes, sizeof(int32_t));
+    st->mail_counter = (uint32_t *)calloc(boxes, sizeof(uint32_t));
+    st->mail_surface = (uint32_t *)calloc(boxes * st->words, sizeof(uint32_t));
+    st->seen = (uint32_t *)calloc(boxes, sizeof(uint32_t));
+    if (!st->mail_seq || !st->mail_trait || !st->mail_counter || !st->mail_surface || !st->seen)
+        return -2;
+    return 0;
+}
+
+static void async_clear(orc_state *st)
+{
+    if (!st->mail_seq) return;
+    const size_t boxes = (size_t)st->n_islands * 4;
+    memset(st->mail_seq, 0, boxes * sizeof(uint32_t));
+    memset(st->mail_trait, 0, boxes * sizeof(int32_t));
+    memset(st->mail_counter, 0, boxes * sizeof(uint32_t));
+    memset(st->mail_surface, 0, boxes * st->words * sizeof(uint32_t));
+    memset(st->seen, 0, boxes * sizeof(uint32_t));
+}
+
+/*
+ * Migration step of island `isl` at its generation g, asynchronous reading:
+ *   1. collect: for d = N, S, E, W the neighbour nb(d)'s mailbox facing isl (its direction
+ *      opposite to d) is taken when it holds a post (sequence > 0) other than the last one
+ *      isl took from d; the four draws of the synchronous mode place the arrivals: a partial
+ *      Fisher-Yates shuffle over all four directions in order (the swap happens whether or
+ *      not direction d delivers) and arrival d, if any, replaces the member in position d;
+ *   2. post: for each d a copy of member e_d = (bits 8..15 of word 3 of slot d's draw) * N
+ *      >> 8 of the island as it stands after step 1 goes to isl's mailbox towards d, whose
+ *      sequence number grows by 2.
+ * arrivals (optional, 4 per island) counts deliveries per direction.
+ */
+static void async_migrate_island(orc_state *st, uint32_t isl, uint32_t g, uint64_t *arrivals)
+{
+    const orc_config *c = &st->cfg;
+    const uint32_t N = c->island_size, words = st->words;
+    uint32_t w3[4];
+    for (uint32_t d = 0; d < 4; ++d) {
+        uint32_t w[4];
+        draw(c->seed, g, isl, d, ORC_PURPOSE_BIRTH, c->run_id, w);
+        w3[d] = w[3];
+    }
+    uint32_t perm[256];
+    for (uint32_t j = 0; j < N; ++j) perm[j] = j;
+    for (uint32_t d = 0; d < 4; ++d) {
+        uint32_t r = d + (uint32_t)((((uint64_t)(w3[d] >> 16)) * (N - d)) >> 16);
+        uint32_t tmp = perm[d];
+        perm[d] = perm[r];
+        perm[r] = tmp;
+        const uint32_t box = neighbour(c, isl, (int)d) * 4 + (d ^ 1u);
+        const uint32_t seq = st->mail_seq[box];
+        if (seq == 0 || seq == st->seen[isl * 4 + d]) continue;
+        st->seen[isl * 4 + d] = seq;
+        const uint32_t dst = isl * N + perm[d];
+        st->trait[dst] = st->mail_trait[box];
+        st->counter[dst] = st->mail_counter[box];
+        memcpy(&st->surface[(size_t)dst * words], &st->mail_surface[(size_t)box * words],
+               words * sizeof(uint32_t));
+        if (tracking(st)) st->tag[dst] = st->mail_tag[box];
+        if (arrivals) arrivals[isl * 4 + d] += 1;
+    }
+    for (uint32_t d = 0; d < 4; ++d) {
+        const uint32_t e = (((w3[d] >> 8) & 0xFFu) * N) >> 8;
+        const uint32_t src = isl * N + e, box = isl * 4 + d;
+        st->mail_trait[box] = st->trait[src];
+        st->mail_counter[box] = st->counter[src];
+        memcpy(&st->mail_surface[(size_t)box * words], &st->surface[(size_t)src * words],
+               words * sizeof(uint32_t));
+        if (tracking(st)) st->mail_tag[box] = st->tag[src];
+        st->mail_seq[box] += 2;
+    }
+}
+
+/*
+ * One window of n_gens generations on the sequential schedule: for each island in index
+ * order, generations gen .. gen + n_gens - 1 (migration step when the migration policy
+ * says so, then evaluation, selection, mutation and deposit -- the deposit site follows
+ * the agent's own counter), after which gen += n_gens.  arrivals as above.
+ * Returns 0, or -2 when out of memory.
+ */
+int orc_step_async(orc_state *st, uint32_t n_gens, uint64_t *arrivals)
+{
+    if (async_alloc(st) != 0 || reserve_events(st, st->gen + n_gens) != 0) return -2;
+    const orc_config *c = &st->cfg;
+    const uint32_t N = c->island_size, words = st->words;
+    for (uint32_t isl = 0; isl < st->n_islands; ++isl) {
+        for (uint32_t i = 0; i < n_gens; ++i) {
+            const uint32_t g = (uint32_t)(st->gen + i);
+            if (c->migrate_every != 0 && g % c->migrate_every == 0)
+                async_migrate_island(st, isl, g, arrivals);
+            reproduce_island(st, isl, g, NULL);
+            /* the island's next population replaces its current one */
+            const size_t base = (size_t)isl * N;
+            memcpy(&st->trait[base], &st->trait2[base], N * sizeof(int32_t));
+            memcpy(&st->counter[base], &st->counter2[base], N * sizeof(uint32_t));
+            memcpy(&st->surface[base * words], &st->surface2[base * words],
+                   (size_t)N * words * sizeof(uint32_t));
+            if (tracking(st)) memcpy(&st->tag[base], &st->tag2[base], N * sizeof(int64_t));
+        }
+    }
+    st->gen += n_gens;
+    return 0;
 }
 
 /* Canonical agent record: int32 trait, uint32 counter, uint32 surface[words], zero padding
@@ -589,6 +767,53 @@ void orc_load(orc_state *st, const void *src, uint64_t generation)
         memcpy(&st->surface[(size_t)a * st->words], rec + 8, 4 * st->words);
     }
     st->gen = generation;
+    async_clear(st);
+    if (tracking(st)) {
+        for (uint32_t a = 0; a < st->n_agents; ++a) st->tag[a] = -1;
+        for (uint32_t k = 0; k < st->n_islands * 4; ++k) st->mail_tag[k] = -1;
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Lineage tracking (test support): the true divergence rank of two agents.              */
+/* ------------------------------------------------------------------------------------ */
+
+/* Start tracking: every current agent (and mailbox) becomes a root of the pedigree.
+   Returns 0, or -2 when out of memory. */
+int orc_track_lineage(orc_state *st)
+{
+    if (tracking(st)) return 0;
+    st->tag = (int64_t *)malloc(st->n_agents * sizeof(int64_t));
+    st->tag2 = (int64_t *)malloc(st->n_agents * sizeof(int64_t));
+    st->mail_tag = (int64_t *)malloc((size_t)st->n_islands * 4 * sizeof(int64_t));
+    if (!st->tag || !st->tag2 || !st->mail_tag) return -2;
+    for (uint32_t a = 0; a < st->n_agents; ++a) st->tag[a] = st->tag2[a] = -1;
+    for (uint32_t k = 0; k < st->n_islands * 4; ++k) st->mail_tag[k] = -1;
+    return 0;
+}
+
+static uint32_t depth_of(const orc_state *st, int64_t e) { return e < 0 ? 0u : st->event_depth[e]; }
+
+/*
+ * D for each pair (i, j), i < j, row-major: the number of births the two agents' lineages
+ * share (their latest common birth's child counter; 0 when they share none).  Deposits of
+ * ranks below D were made once for both; the deposit of rank D, if both reach it, was drawn
+ * in two separate births.  Returns 0, or -1 when tracking is off.
+ */
+int orc_divergence(const orc_state *st, const uint32_t *ids, uint32_t n, uint32_t *out)
+{
+    if (!tracking(st)) return -1;
+    uint64_t p = 0;
+    for (uint32_t i = 0; i < n; ++i)
+        for (uint32_t j = i + 1; j < n; ++j, ++p) {
+            int64_t a = st->tag[ids[i]], b = st->tag[ids[j]];
+            while (a != b) {
+                if (depth_of(st, a) >= depth_of(st, b)) a = st->event_parent[a];
+                else b = st->event_parent[b];
+            }
+            out[p] = depth_of(st, a);
+        }
+    return 0;
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -65,6 +65,12 @@ def _load():
     lib.orc_mrca_bounds_mixed.argtypes = [C.c_void_p, C.c_uint32, u32p, C.c_uint32, C.c_uint32,
                                           C.c_uint32, C.c_uint32, u32p, u32p]
     lib.orc_mrca_bounds_mixed.restype = C.c_int
+    lib.orc_step_async.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p]
+    lib.orc_step_async.restype = C.c_int
+    lib.orc_track_lineage.argtypes = [C.c_void_p]
+    lib.orc_track_lineage.restype = C.c_int
+    lib.orc_divergence.argtypes = [C.c_void_p, u32p, C.c_uint32, u32p]
+    lib.orc_divergence.restype = C.c_int
     lib.orc_openmp_enabled.argtypes = []
     lib.orc_openmp_enabled.restype = C.c_int
     _lib = lib
@@ -182,7 +188,8 @@ def openmp_enabled():
 
 
 class OracleRun:
-    """One synchronous GA run held by the C oracle."""
+    """One GA run held by the C oracle: synchronous generations (step, migrate, reproduce)
+    or the asynchronous mode on its sequential schedule (step_async)."""
 
     def __init__(self, rows, cols, island_size=32, tournament_size=5, p_ben=0.01, p_del=0.01,
                  surface_sites=64, differentia_bits=1, curation=STEADY, migrate_every=1,
@@ -195,6 +202,7 @@ class OracleRun:
         if not self._st:
             raise ValueError("invalid oracle config")
         self.n_agents = int(self._lib.orc_agent_count(self._st))
+        self.n_islands = rows * cols
         self.record_bytes = int(self._lib.orc_record_bytes(self._st))
 
     def close(self):
@@ -214,6 +222,37 @@ class OracleRun:
 
     def step(self, n_gens):
         self._lib.orc_step(self._st, n_gens)
+
+    def step_async(self, n_gens, window=16):
+        """Asynchronous mode on the sequential schedule: windows of `window` generations
+        (the last one shorter), each run island by island in index order.  Returns the
+        number of arrivals per (island, direction) as an (n_islands, 4) array."""
+        arrivals = np.zeros((self.n_islands, 4), np.uint64)
+        left = int(n_gens)
+        while left > 0:
+            w = min(window, left)
+            rc = self._lib.orc_step_async(self._st, w, arrivals.ctypes.data)
+            if rc != 0:
+                raise MemoryError("oracle: out of memory")
+            left -= w
+        return arrivals
+
+    def track_lineage(self):
+        """Record every birth from now on (call at generation 0) so that divergence() can
+        report true divergence ranks."""
+        if self._lib.orc_track_lineage(self._st) != 0:
+            raise MemoryError("oracle: out of memory")
+
+    def divergence(self, ids):
+        """True divergence rank D of each pair (i < j, row-major) of the given agents: the
+        number of births their lineages share."""
+        ids_a, idp = _u32(ids)
+        n = len(ids_a)
+        out = np.zeros(n * (n - 1) // 2, np.uint32)
+        if self._lib.orc_divergence(self._st, idp, n,
+                                    out.ctypes.data_as(C.POINTER(C.c_uint32))) != 0:
+            raise ValueError("lineage tracking is off")
+        return out
 
     def migrate(self):
         """Apply this generation's migration; return the source id of every slot."""

@@ -1,0 +1,136 @@
+"""Pins for the oracle's asynchronous mode (Sec. 2: migrants are posted and collected without
+waiting) on its sequential schedule, and for the lineage tracking the pins rely on.
+
+What fixes the asynchronous mode independently of its own code:
+  - with migration off it must be the synchronous GA exactly (the reproduction path);
+  - the number of deliveries per (island, direction) follows from the protocol alone (a post
+    is taken once, by its neighbour's next migration step): within each window an earlier
+    neighbour delivers once, a later one delivers its previous window's post, and an island
+    that is its own neighbour delivers every generation but the very first;
+  - on populations it produces, whose counters drift apart, the mixed-counter MRCA bounds
+    must bracket the true divergence rank known from the recorded pedigree.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import OracleRun, STEADY, TILTED, HYBRID
+
+
+def _neighbour(rows, cols, isl, d):
+    y, x = divmod(isl, cols)
+    if d == 0:
+        y = (y - 1) % rows
+    elif d == 1:
+        y = (y + 1) % rows
+    elif d == 2:
+        x = (x + 1) % cols
+    else:
+        x = (x - 1) % cols
+    return y * cols + x
+
+
+@pytest.mark.parametrize("window", [1, 5, 16])
+@pytest.mark.parametrize("N,S,b,policy", [(16, 64, 1, STEADY), (32, 32, 8, TILTED)])
+def test_no_migration_is_sync(window, N, S, b, policy):
+    kw = dict(island_size=N, surface_sites=S, differentia_bits=b, curation=policy,
+              migrate_every=0, seed=9, p_ben=0.05, p_del=0.05)
+    a = OracleRun(3, 4, **kw)
+    s = OracleRun(3, 4, **kw)
+    a.step_async(37, window=window)
+    s.step(37)
+    assert a.generation == s.generation == 37
+    assert np.array_equal(a.snapshot(), s.snapshot())
+
+
+@pytest.mark.parametrize("rows,cols", [(1, 1), (1, 3), (3, 1), (2, 2), (3, 4), (1, 2)])
+@pytest.mark.parametrize("window", [1, 3, 8])
+def test_arrival_counts(rows, cols, window):
+    k = 4
+    run = OracleRun(rows, cols, island_size=16, seed=3)
+    arr = run.step_async(k * window, window=window)
+    for isl in range(rows * cols):
+        for d in range(4):
+            nb = _neighbour(rows, cols, isl, d)
+            want = k if nb < isl else k - 1 if nb > isl else k * window - 1
+            assert arr[isl, d] == want, (isl, d, nb, arr[isl, d], want)
+
+
+def test_counters_drift_and_stay_consistent():
+    """Arrivals keep their counters, so counters spread; each birth still adds one to the
+    counter and changes the trait by at most one."""
+    run = OracleRun(3, 3, island_size=16, seed=21, p_ben=0.2, p_del=0.2)
+    run.step_async(96, window=8)
+    c = run.counters().astype(np.int64)
+    t = run.traits().astype(np.int64)
+    assert c.max() > c.min()
+    assert np.all(np.abs(t) <= c)
+
+
+def test_tracking_matches_pedigree_sync():
+    """Lineage tags against a pedigree rebuilt from the synchronous migrate / reproduce
+    outputs (source ids and winner slots)."""
+    R, Cc, N, G = 3, 3, 8, 120
+    run = OracleRun(R, Cc, island_size=N, seed=13)
+    run.track_lineage()
+    n = run.n_agents
+    parents = []
+    for _ in range(G):
+        src = run.migrate()
+        par = run.reproduce()
+        parents.append(src[(np.arange(n) // N) * N + par])
+    ids = np.arange(0, n, 3, dtype=np.uint32)
+    D = run.divergence(ids)
+
+    def divergence(a, b):
+        for t in range(G, 0, -1):
+            if a == b:
+                return t
+            a, b = parents[t - 1][a], parents[t - 1][b]
+        return 0
+
+    p = 0
+    for i in range(len(ids)):
+        for j in range(i + 1, len(ids)):
+            assert D[p] == divergence(int(ids[i]), int(ids[j]))
+            p += 1
+
+
+@pytest.mark.parametrize("policy,S,b,window,every", [
+    (STEADY, 64, 1, 8, 1), (TILTED, 32, 8, 16, 1), (HYBRID, 64, 1, 4, 1),
+    (STEADY, 256, 1, 32, 1), (STEADY, 64, 1, 8, 20), (TILTED, 32, 8, 8, 20)])
+def test_async_mrca_brackets_true_divergence(policy, S, b, window, every):
+    """every = 20: sparse migration keeps deep splits (D spread over the whole run)."""
+    run = OracleRun(4 if every > 1 else 3, 4 if every > 1 else 3, island_size=16,
+                    surface_sites=S, differentia_bits=b, curation=policy, seed=31 + S,
+                    migrate_every=every)
+    run.track_lineage()
+    run.step_async(400 if every == 1 else 300, window=window)
+    rec = run.snapshot()
+    cnt = run.counters()
+    ids = np.sort(np.random.default_rng(2).choice(run.n_agents, 80, replace=False)).astype(np.uint32)
+    assert len(np.unique(cnt[ids])) > 1  # the case the mixed bounds exist for
+    lo, hi = oracle.mrca_bounds_mixed(rec, ids, policy, S, b)
+    D = run.divergence(ids)
+    p, misses = 0, 0
+    for i in range(len(ids)):
+        for j in range(i + 1, len(ids)):
+            Ta, Tb = int(cnt[ids[i]]), int(cnt[ids[j]])
+            assert lo[p] <= hi[p] <= min(Ta, Tb)
+            assert D[p] <= hi[p], (ids[i], ids[j], D[p], lo[p], hi[p])
+            misses += D[p] < lo[p]
+            p += 1
+    assert misses / p < 0.10
+
+
+def test_load_clears_mailboxes():
+    kw = dict(island_size=16, seed=4)
+    a = OracleRun(2, 3, **kw)
+    a.step_async(20, window=4)
+    snap = a.snapshot()
+    a.load(snap, 20)
+    a.step_async(12, window=4)
+    b = OracleRun(2, 3, **kw)
+    b.load(snap, 20)
+    b.step_async(12, window=4)
+    assert np.array_equal(a.snapshot(), b.snapshot())

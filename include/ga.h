@@ -56,7 +56,16 @@ extern "C" {
 #define GA_TILTED 1u /* recency-weighted: two ranks per hanoi level, S/2 levels           */
 #define GA_HYBRID 2u /* first S/2 sites steady on even ranks, last S/2 tilted on odd ranks */
 
-#define GA_SYNC 0u /* synchronous generations: deterministic, bit-exact                  */
+#define GA_SYNC 0u  /* synchronous generations: deterministic, bit-exact                 */
+#define GA_ASYNC 1u /* asynchronous migration through per-island mailboxes (Sec. 2 WSE loop):
+                       islands advance without waiting for one another, so results depend on
+                       scheduling and agents' counters drift apart                         */
+#define GA_ASYNC_SEQUENTIAL 2u /* the GA_ASYNC step on a reproducible schedule: within each
+                       window of generations, islands run one at a time in index order
+                       (one launch per island; slow; for debugging and checking)            */
+
+/* Largest asynchronous window (generations one island runs per launch). */
+#define GA_ASYNC_MAX_WINDOW 256u
 
 /* Genome model: what the first record word means and how it mutates. */
 #define GA_MODEL_TRAIT 0u   /* int32 trait; +1 with p_ben, -1 with p_del                     */
@@ -76,7 +85,7 @@ typedef struct ga_config {
     uint32_t surface_sites;     /* S: power of two, >= 4 (>= 8 for GA_HYBRID)                 */
     uint32_t differentia_bits;  /* b in {1, 2, 4, 8}; S * b <= 256                            */
     uint32_t curation;          /* GA_STEADY / GA_TILTED / GA_HYBRID                          */
-    uint32_t mode;              /* GA_SYNC                                                    */
+    uint32_t mode;              /* GA_SYNC / GA_ASYNC / GA_ASYNC_SEQUENTIAL                   */
     uint64_t seed;              /* Philox key = (low 32 bits, high 32 bits)                   */
     uint32_t run_id;            /* fourth Philox counter word: distinct runs draw disjointly  */
     uint32_t model;             /* GA_MODEL_TRAIT / GA_MODEL_FITNESS                          */
@@ -95,7 +104,9 @@ int ga_config_check(const ga_config *cfg);
 /* Bytes of one canonical agent record for cfg (16, 32 or 48). */
 int ga_record_bytes(const ga_config *cfg, uint32_t *bytes);
 
-/* Bytes of device workspace a run of cfg needs (two population buffers plus a header). */
+/* Bytes of device workspace a run of cfg needs (two population buffers plus a header; in the
+   asynchronous modes also four mailboxes of 16 + record_bytes bytes and four 4-byte
+   sequence marks per island). */
 int ga_workspace_bytes(const ga_config *cfg, size_t *bytes);
 
 /*
@@ -118,6 +129,30 @@ int ga_reset(ga_run *run);
  * migration); every_k >= 1.  The default after ga_create is (1, 1).
  */
 int ga_migrate_policy(ga_run *run, uint32_t per_neighbor, uint32_t every_k);
+
+/*
+ * Asynchronous modes (Sec. 2: the wafer-scale loop posts and collects migrants without
+ * waiting).  Each island owns one outgoing mailbox per direction (a sequence word and one
+ * record).  On each of its migration generations g (g mod every_k == 0) an island, in this
+ * order: (1) for directions N, S, E, W takes the record its neighbour last posted towards
+ * it, if the neighbour posted since the island last looked and the mailbox is not being
+ * written at that moment (otherwise nothing arrives from that direction); arrivals land in
+ * slots chosen by the same partial Fisher-Yates draw as in GA_SYNC, missing arrivals
+ * leaving their slot alone; (2) posts a copy of member e_d = (bits 8..15 of word 3 of its
+ * slot-d birth draw) * N >> 8 of its population to its mailbox towards d; then (3)
+ * reproduces as in GA_SYNC.  Nothing ever waits.  A migrant keeps its counter, so the
+ * counters of an island's agents drift apart and each deposit uses the site of the
+ * agent's own counter.
+ *
+ * A launch runs `window` generations of every island (all islands start it at the same
+ * generation); neighbours that run in the same launch exchange migrants at most about a
+ * window apart.  GA_ASYNC_SEQUENTIAL runs each window island by island in index order: a
+ * reproducible schedule the CPU model follows exactly.  window in [1, GA_ASYNC_MAX_WINDOW];
+ * the default after ga_create is 16.  Mailboxes and sequence marks are cleared by
+ * ga_create, ga_reset and ga_load.  Errors: GA_EINVAL (window out of range),
+ * GA_ESTATE (run not in an asynchronous mode).
+ */
+int ga_async_window(ga_run *run, uint32_t window);
 
 /*
  * Enqueue n_gens generations on the run's stream (Sec. 2 generational cycle, halting after
@@ -156,23 +191,30 @@ int ga_load(ga_run *run, const void *host_src, size_t bytes, uint64_t generation
  * Pairwise MRCA bounds (Fig. 1: post hoc relatedness from hstrat markers).
  * agent_ids: n distinct agent ids (host); lo, hi: n(n-1)/2 uint32 each (host), pairs (i, j),
  * i < j, in row-major upper-triangle order: pair index i*(2n-i-1)/2 + (j-i-1).
- * All sampled agents must hold the same counter T (always true in GA_SYNC mode).  With the
+ * In GA_SYNC mode all sampled agents must hold the same counter T.  With the
  * sites' retained ranks r_1 < ... < r_m (ranks < T) and i* the first index at which the
  * two differentiae differ, the divergence rank D (first rank the two lineages drew in
  * separate births) satisfies D in [lo, hi]:
  *   hi = r_{i*} (certain), lo = r_{i*-K} + 1 or 0 if i* <= K; with no mismatch hi = T and
  *   lo = r_{m-K+1} + 1 (0 if m < K); K = smallest integer with 2^(-bK) < 0.05, so lo holds
  *   with confidence 0.95.
+ * In the asynchronous modes agents i and j may hold different counters Ti and Tj: the
+ * ranks compared are those retained by both (a rank sits at the same site in both tables,
+ * so these are the sites whose rank tables at Ti and Tj agree), in ascending order, and the
+ * same rule applies to that list with hi = min(Ti, Tj) when nothing mismatches.  Cost
+ * O(Tmin + n (Tmax - Tmin)) curation evaluations for the rank tables (Tmin, Tmax: the
+ * smallest and largest sampled counter) plus O(n^2 S) for the pairs.
  * Synchronous.  Scratch memory is allocated and freed on the run's stream.
  * Errors: GA_EINVAL (n < 2, n > 65536, id out of range, null pointers), GA_ESTATE
- * (counters differ), GA_ENOMEM, GA_ECUDA.
+ * (GA_SYNC mode and counters differ), GA_ENOMEM, GA_ECUDA.
  */
 int ga_mrca_bounds(ga_run *run, const uint32_t *agent_ids, uint32_t n, uint32_t *lo,
                    uint32_t *hi);
 
 /* As ga_mrca_bounds with device buffers for ids, lo and hi; asynchronous on the run's
    stream.  Ids are not range-checked on the host (the kernel skips out-of-range ids and
-   records GA_EINVAL, reported by ga_sync), counter mismatches are reported by ga_sync. */
+   records GA_EINVAL, reported by ga_sync), counter mismatches (GA_SYNC mode) are reported
+   by ga_sync. */
 int ga_mrca_bounds_device(ga_run *run, const uint32_t *d_agent_ids, uint32_t n,
                           uint32_t *d_lo, uint32_t *d_hi);
 
@@ -189,8 +231,9 @@ int ga_mrca_bounds_device(ga_run *run, const uint32_t *d_agent_ids, uint32_t n,
  * on a member (ga_snapshot, ga_mrca_bounds, ga_step, ga_reset, ga_load, ...); a member whose
  * generation or buffer changed through such calls is picked up by the next ga_batch_step.  Member runs may have different shapes, mutation rates, tournament
  * sizes, curation policies, seeds and migration policies.  Members with 65,536 islands or
- * more, float-fitness runs and island sizes without a batched kernel (4, 128) step with the
- * single-run kernels on the batch's stream instead of sharing class launches.
+ * more, float-fitness runs, asynchronous runs and island sizes without a batched kernel
+ * (4, 128) step with the single-run kernels on the batch's stream instead of sharing class
+ * launches.
  */
 typedef struct ga_batch ga_batch;
 

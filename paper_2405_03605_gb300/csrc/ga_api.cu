@@ -51,12 +51,14 @@ int check_config(const ga_config *c)
     if (c->curation > GA_HYBRID) return GA_EINVAL;
     if (c->surface_sites < (c->curation == GA_HYBRID ? 8u : 4u)) return GA_EINVAL;
     if (static_cast<uint64_t>(c->surface_sites) * b > 256u) return GA_EINVAL;
-    if (c->mode != GA_SYNC || c->model > GA_MODEL_FITNESS) return GA_EINVAL;
+    if (c->mode > GA_ASYNC_SEQUENTIAL || c->model > GA_MODEL_FITNESS) return GA_EINVAL;
     if (c->model == GA_MODEL_FITNESS && !(c->effect_scale > 0.0 && c->effect_scale < 1e30))
         return GA_EINVAL;
     const uint64_t agents = static_cast<uint64_t>(c->rows) * c->cols * c->island_size;
     if (agents > 0xFFFFFFFFull) return GA_EINVAL;
     if (!ga::step_supported(c->island_size, surface_words_of(c), c->model)) return GA_EUNSUPPORTED;
+    if (c->mode != GA_SYNC && !ga::async_supported(c->island_size, surface_words_of(c), c->model))
+        return GA_EUNSUPPORTED;
     return GA_OK;
 }
 
@@ -68,6 +70,23 @@ size_t population_bytes(const ga_config *c)
 }
 
 size_t buffer_stride(const ga_config *c) { return align_up(population_bytes(c), 256); }
+
+// Workspace: header, two population buffers, then (asynchronous modes) mailboxes and marks.
+size_t workspace_need(const ga_config *c)
+{
+    size_t need = ga::kHeaderBytes + 2 * buffer_stride(c);
+    if (c->mode != GA_SYNC) need += ga::async_state_bytes(c->rows * c->cols, record_bytes_of(c));
+    return need;
+}
+
+// Clear the mailboxes and sequence marks (asynchronous modes).
+int clear_async_state(ga_run *run)
+{
+    if (!run->mail) return GA_OK;
+    const cudaError_t e = cudaMemsetAsync(
+        run->mail, 0, ga::async_state_bytes(run->n_islands, run->record_bytes), run->stream);
+    return e == cudaSuccess ? GA_OK : GA_ECUDA;
+}
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? GA_OK : GA_ECUDA; }
 
@@ -91,6 +110,7 @@ namespace ga {
 
 int step_run(ga_run *run, uint32_t n_gens, cudaStream_t stream)
 {
+    if (run->cfg.mode != GA_SYNC) return async_step(run, n_gens, stream);
     if (run->generation + n_gens > 0xFFFFFFFFull) return GA_EINVAL;
     while (n_gens > 0) {
         // curation sites of the next chunk of generations, computed on the device once
@@ -164,7 +184,7 @@ int ga_workspace_bytes(const ga_config *cfg, size_t *bytes)
     if (!cfg || !bytes) return GA_EINVAL;
     const int rc = check_config(cfg);
     if (rc != GA_OK) return rc;
-    *bytes = ga::kHeaderBytes + 2 * buffer_stride(cfg);
+    *bytes = workspace_need(cfg);
     return GA_OK;
 }
 
@@ -174,7 +194,7 @@ int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_
     *out = nullptr;
     int rc = check_config(cfg);
     if (rc != GA_OK) return rc;
-    const size_t need = ga::kHeaderBytes + 2 * buffer_stride(cfg);
+    const size_t need = workspace_need(cfg);
     if (workspace) {
         if (workspace_bytes < need) return GA_ENOMEM;
         if (reinterpret_cast<uintptr_t>(workspace) % 256u != 0u) return GA_EINVAL;
@@ -214,7 +234,17 @@ int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_
     run->pop[0] = base + ga::kHeaderBytes;
     run->pop[1] = base + ga::kHeaderBytes + buffer_stride(cfg);
     run->cur = 0;
+    run->mail = nullptr;
+    run->seen = nullptr;
+    run->async_window = 16;
+    if (cfg->mode != GA_SYNC) {
+        const size_t mail_bytes = align_up(static_cast<size_t>(run->n_islands) * 4u *
+                                               (16u + run->record_bytes), 256);
+        run->mail = base + ga::kHeaderBytes + 2 * buffer_stride(cfg);
+        run->seen = reinterpret_cast<uint32_t *>(run->mail + mail_bytes);
+    }
     rc = cuda_rc(cudaMemsetAsync(base, 0, ga::kHeaderBytes, run->stream));
+    if (rc == GA_OK) rc = clear_async_state(run);
     if (rc == GA_OK) rc = cuda_rc(ga::launch_founder(run, run->pop[0]));
     if (rc != GA_OK) {
         if (run->owns_workspace) cudaFree(run->workspace);
@@ -230,6 +260,8 @@ int ga_reset(ga_run *run)
     if (!run) return GA_EINVAL;
     run->cur = 0;
     run->generation = 0;
+    const int rc = clear_async_state(run);
+    if (rc != GA_OK) return rc;
     return cuda_rc(ga::launch_founder(run, run->pop[0]));
 }
 
@@ -238,6 +270,14 @@ int ga_migrate_policy(ga_run *run, uint32_t per_neighbor, uint32_t every_k)
     if (!run || per_neighbor > 1u || every_k == 0u) return GA_EINVAL;
     run->per_neighbor = per_neighbor;
     run->every_k = every_k;
+    return GA_OK;
+}
+
+int ga_async_window(ga_run *run, uint32_t window)
+{
+    if (!run || window == 0u || window > GA_ASYNC_MAX_WINDOW) return GA_EINVAL;
+    if (run->cfg.mode == GA_SYNC) return GA_ESTATE;
+    run->async_window = window;
     return GA_OK;
 }
 
@@ -306,6 +346,7 @@ int ga_load(ga_run *run, const void *host_src, size_t bytes, uint64_t generation
     if (cudaMemcpyAsync(run->pop[run->cur], host_src, bytes, cudaMemcpyHostToDevice,
                         run->stream) != cudaSuccess)
         return GA_ECUDA;
+    if (clear_async_state(run) != GA_OK) return GA_ECUDA;
     if (cudaStreamSynchronize(run->stream) != cudaSuccess) return GA_ECUDA;
     run->generation = generation;
     return GA_OK;

@@ -163,12 +163,14 @@ uint32_t ts_class(uint32_t tsize) { return tsize == 5 ? 5 : 0; }
 
 // Members this large fill the GPU on their own: they step with the single-run kernels (their
 // round keys and parameters in the constant bank) instead of joining a class launch; so do
-// members of a model or island size the batched kernels do not cover.
+// asynchronous members and members of a model or island size the batched kernels do not
+// cover.
 constexpr uint32_t kSoloIslands = 1u << 16;
 
 bool solo(const ga_run *r)
 {
     return r->n_islands >= kSoloIslands || r->cfg.model != GA_MODEL_TRAIT ||
+           r->cfg.mode != GA_SYNC ||
            !pick(r->cfg.island_size, sw_class(r->surface_words), 0, 8);
 }
 

@@ -29,6 +29,10 @@ struct ga_run {
     uint64_t sites_base;
     uint8_t *pop[2];     // double-buffered population
     int cur;             // index of the current population buffer
+    // asynchronous modes only (null otherwise)
+    uint8_t *mail;       // [island][direction] mailboxes: 16-byte sequence word, record
+    uint32_t *seen;      // [island][direction] last sequence taken from that neighbour
+    uint32_t async_window;
 };
 
 namespace ga {
@@ -56,6 +60,15 @@ int step_run(ga_run *run, uint32_t n_gens, cudaStream_t stream);
 cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t *d_lo,
                         uint32_t *d_hi, void *scratch);
 size_t mrca_scratch_bytes(const ga_run *run, uint32_t n);
+// Asynchronous mode (ga_async.cu).
+bool async_supported(uint32_t island_size, uint32_t surface_words, uint32_t model);
+size_t async_state_bytes(uint32_t n_islands, uint32_t record_bytes);
+// Generations [g0, g0 + n_gens) of islands [first, last), reading src and writing dst.
+cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_t g0,
+                                uint32_t n_gens, uint32_t first, uint32_t last,
+                                cudaStream_t stream);
+int async_step(ga_run *run, uint32_t n_gens, cudaStream_t stream);
+
 cudaError_t launch_curation_sites(uint32_t policy, uint32_t sites, uint32_t t0, uint32_t count,
                                   int32_t *d_sites, cudaStream_t stream);
 

@@ -202,17 +202,211 @@ uint32_t margin(uint32_t bits)
     return K;
 }
 
+// ---------------------------------------------------------------------------------------
+// Mixed counters (asynchronous runs): agents i and j may hold different counters Ti, Tj.  A
+// rank, once deposited, stays at its own site until overwritten, so the ranks retained at
+// both counters are exactly the sites whose holder tables at Ti and Tj agree.
+//   1. counter_kernel: each sampled agent's counter; Tmin and Tmax (atomicMin / atomicMax).
+//   2. base_kernel   : holder table at Tmin, replaying ranks 0 .. Tmin - 1 (as rank_kernel).
+//   3. table_kernel  : one block per sampled agent: base table plus ranks Tmin .. Ti - 1, in
+//                      shared memory; table row i (rank + 1 per site, 0: empty).
+//   4. mixed_pair_kernel: 16 x 16 pairs per block with the 32 agents' tables and surfaces in
+//                      shared memory; one thread per pair makes two passes over the sites:
+//                      (a) the smallest common rank whose differentiae differ (hi), (b) the
+//                      K largest common ranks below it (lo = the K-th + 1).
+// ---------------------------------------------------------------------------------------
+constexpr int kMixTile = 16;
+
+struct MixedLayout {
+    uint32_t *meta;    // [0] Tmin, [1] Tmax
+    uint32_t *holder;  // [S] base table at Tmin
+    uint32_t *cnt;     // [n] counters of the sampled agents
+    uint32_t *tables;  // [n][S] rank + 1 held by each site at the agent's counter
+};
+
+size_t mixed_scratch_bytes(uint32_t S, uint32_t n)
+{
+    return 256 + align_up(S * 4u, 256) + align_up(static_cast<size_t>(n) * 4u, 256) +
+           align_up(static_cast<size_t>(n) * S * 4u, 256);
+}
+
+MixedLayout carve_mixed(void *scratch, uint32_t S, uint32_t n)
+{
+    uint8_t *p = static_cast<uint8_t *>(scratch);
+    MixedLayout l;
+    l.meta = reinterpret_cast<uint32_t *>(p);
+    size_t off = 256;
+    l.holder = reinterpret_cast<uint32_t *>(p + off);
+    off += align_up(S * 4u, 256);
+    l.cnt = reinterpret_cast<uint32_t *>(p + off);
+    off += align_up(static_cast<size_t>(n) * 4u, 256);
+    l.tables = reinterpret_cast<uint32_t *>(p + off);
+    return l;
+}
+
+__global__ void counter_kernel(const uint32_t *__restrict__ pop, uint32_t record_words,
+                               uint32_t n_agents, const uint32_t *__restrict__ ids, uint32_t n,
+                               uint32_t *__restrict__ cnt, uint32_t *__restrict__ meta,
+                               int *__restrict__ status)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t id = ids[i];
+    uint32_t c = 0;
+    if (id >= n_agents) atomicCAS(status, GA_OK, GA_EINVAL);
+    else c = pop[static_cast<size_t>(id) * record_words + 1];
+    cnt[i] = c;
+    atomicMin(&meta[0], c);
+    atomicMax(&meta[1], c);
+}
+
+__global__ void base_kernel(uint32_t *__restrict__ holder, const uint32_t *__restrict__ meta,
+                            uint32_t policy, uint32_t log2_sites, uint32_t sites)
+{
+    const uint32_t T = meta[0];
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        const int site = curation_site(policy, log2_sites, sites, t);
+        if (site >= 0) atomicMax(&holder[site], t + 1u);
+    }
+}
+
+__global__ void table_kernel(const uint32_t *__restrict__ holder, const uint32_t *__restrict__ meta,
+                             const uint32_t *__restrict__ cnt, uint32_t *__restrict__ tables,
+                             uint32_t policy, uint32_t log2_sites, uint32_t sites)
+{
+    __shared__ uint32_t h[256];
+    const uint32_t i = blockIdx.x;
+    for (uint32_t k = threadIdx.x; k < sites; k += blockDim.x) h[k] = holder[k];
+    __syncthreads();
+    const uint32_t T = cnt[i];
+    for (uint32_t t = meta[0] + threadIdx.x; t < T; t += blockDim.x) {
+        const int site = curation_site(policy, log2_sites, sites, t);
+        if (site >= 0) atomicMax(&h[site], t + 1u);
+    }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < sites; k += blockDim.x)
+        tables[static_cast<size_t>(i) * sites + k] = h[k];
+}
+
+// Block (x, y): rows i in tile y, columns j in tile x (tiles below the diagonal exit).
+__global__ void __launch_bounds__(kMixTile * kMixTile)
+mixed_pair_kernel(const uint32_t *__restrict__ pop, uint32_t record_words, uint32_t n_agents,
+                  const uint32_t *__restrict__ ids, uint32_t n, const uint32_t *__restrict__ cnt,
+                  const uint32_t *__restrict__ tables, uint32_t sites, uint32_t bits, uint32_t K,
+                  uint32_t *__restrict__ lo, uint32_t *__restrict__ hi)
+{
+    constexpr int kSurfPad = kPackWords + 1;
+    __shared__ uint32_t tab[2 * kMixTile][256 + 1];
+    __shared__ uint32_t surf[2 * kMixTile][kSurfPad];
+    __shared__ uint32_t count[2 * kMixTile];
+    if (blockIdx.x < blockIdx.y) return;  // uniform across the block
+    const uint32_t i0 = blockIdx.y * kMixTile, j0 = blockIdx.x * kMixTile;
+    // rows 0..15: agents i0 + r; rows 16..31: agents j0 + r
+    for (uint32_t idx = threadIdx.x; idx < 2u * kMixTile * sites; idx += blockDim.x) {
+        const uint32_t row = idx / sites, k = idx - row * sites;
+        const uint32_t a = row < kMixTile ? i0 + row : j0 + row - kMixTile;
+        tab[row][k] = a < n ? tables[static_cast<size_t>(a) * sites + k] : 0u;
+    }
+    for (uint32_t idx = threadIdx.x; idx < 2u * kMixTile * kPackWords; idx += blockDim.x) {
+        const uint32_t row = idx / kPackWords, w = idx - row * kPackWords;
+        const uint32_t a = row < kMixTile ? i0 + row : j0 + row - kMixTile;
+        uint32_t v = 0;
+        if (a < n && w + 2u < record_words) {
+            const uint32_t id = ids[a];
+            if (id < n_agents) v = pop[static_cast<size_t>(id) * record_words + 2u + w];
+        }
+        surf[row][w] = v;
+    }
+    if (threadIdx.x < 2u * kMixTile) {
+        const uint32_t row = threadIdx.x;
+        const uint32_t a = row < kMixTile ? i0 + row : j0 + row - kMixTile;
+        count[row] = a < n ? cnt[a] : 0u;
+    }
+    __syncthreads();
+
+    const uint32_t ty = threadIdx.x / kMixTile, tx = threadIdx.x % kMixTile;
+    const uint32_t i = i0 + ty, j = j0 + tx;
+    if (!(i < j && j < n)) return;
+    const uint32_t *ta = tab[ty], *tb = tab[kMixTile + tx];
+    const uint32_t *sa = surf[ty], *sb = surf[kMixTile + tx];
+    const uint32_t dmask = (1u << bits) - 1u;
+
+    // (a) smallest common rank (+1) whose differentiae differ
+    bool mismatch = false;
+    uint32_t hmin = 0xFFFFFFFFu;
+    for (uint32_t k = 0; k < sites; ++k) {
+        const uint32_t va = ta[k];
+        if (va == 0u || va != tb[k]) continue;
+        const uint32_t pos = k * bits;
+        const uint32_t da = (sa[pos >> 5] >> (pos & 31u)) & dmask;
+        const uint32_t db = (sb[pos >> 5] >> (pos & 31u)) & dmask;
+        if (da != db && (!mismatch || va < hmin)) {
+            hmin = va;
+            mismatch = true;
+        }
+    }
+    // (b) the K largest common ranks (+1) below it, descending
+    uint32_t top[5] = {0u, 0u, 0u, 0u, 0u};
+    for (uint32_t k = 0; k < sites; ++k) {
+        uint32_t v = ta[k];
+        if (v == 0u || v != tb[k] || (mismatch && v >= hmin)) continue;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const uint32_t t = top[q];
+            const bool up = v > t;
+            top[q] = up ? v : t;
+            v = up ? t : v;
+        }
+    }
+    const uint32_t Ta = count[ty], Tb = count[kMixTile + tx];
+    const uint32_t h = mismatch ? hmin - 1u : (Ta < Tb ? Ta : Tb);
+    const uint32_t l = top[K - 1u];  // rank + 1 of the K-th largest, 0 if fewer than K
+    const size_t p = static_cast<size_t>(i) * (2ull * n - i - 1ull) / 2ull + (j - i - 1u);
+    __stcs(&lo[p], l);
+    __stcs(&hi[p], h);
+}
+
 }  // namespace
 
 size_t mrca_scratch_bytes(const ga_run *run, uint32_t n)
 {
     const size_t S = run->cfg.surface_sites;
+    if (run->cfg.mode != GA_SYNC) return mixed_scratch_bytes(static_cast<uint32_t>(S), n);
     return 3 * align_up(S * 4, 256) + 256 + static_cast<size_t>(n) * kPackWords * 4 + 256;
 }
+
+namespace {
+
+cudaError_t launch_mrca_mixed(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t *d_lo,
+                              uint32_t *d_hi, void *scratch)
+{
+    const uint32_t S = run->cfg.surface_sites, b = run->cfg.differentia_bits;
+    const uint32_t policy = run->cfg.curation;
+    MixedLayout l = carve_mixed(scratch, S, n);
+    cudaError_t e = cudaMemsetAsync(l.meta, 0xFF, sizeof(uint32_t), run->stream);  // Tmin
+    if (e == cudaSuccess) e = cudaMemsetAsync(l.meta + 1, 0, sizeof(uint32_t), run->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(l.holder, 0, S * sizeof(uint32_t), run->stream);
+    if (e != cudaSuccess) return e;
+    const uint32_t *pop = reinterpret_cast<const uint32_t *>(run->pop[run->cur]);
+    const uint32_t rw = run->record_bytes / 4u;
+    counter_kernel<<<(n + 255u) / 256u, 256, 0, run->stream>>>(pop, rw, run->n_agents, d_ids, n,
+                                                               l.cnt, l.meta, run->d_status);
+    base_kernel<<<608, 256, 0, run->stream>>>(l.holder, l.meta, policy, run->log2_sites, S);
+    table_kernel<<<n, 256, 0, run->stream>>>(l.holder, l.meta, l.cnt, l.tables, policy,
+                                             run->log2_sites, S);
+    const uint32_t tiles = (n + kMixTile - 1) / kMixTile;
+    mixed_pair_kernel<<<dim3(tiles, tiles), kMixTile * kMixTile, 0, run->stream>>>(
+        pop, rw, run->n_agents, d_ids, n, l.cnt, l.tables, S, b, margin(b), d_lo, d_hi);
+    run->launches += 4;
+    return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t *d_lo,
                         uint32_t *d_hi, void *scratch)
 {
+    if (run->cfg.mode != GA_SYNC) return launch_mrca_mixed(run, d_ids, n, d_lo, d_hi, scratch);
     const uint32_t S = run->cfg.surface_sites, b = run->cfg.differentia_bits;
     const uint32_t T = static_cast<uint32_t>(run->generation);
     MrcaLayout l = carve(scratch, S, n);

@@ -19,6 +19,7 @@ LIB_PATH = os.environ.get("PAPER_2405_03605_GB300_LIB") or os.path.join(
 GA_OK = 0
 STEADY, TILTED, HYBRID = 0, 1, 2
 MODEL_TRAIT, MODEL_FITNESS = 0, 1
+SYNC, ASYNC, ASYNC_SEQUENTIAL = 0, 1, 2
 
 EXPORTED = (
     "ga_config_default", "ga_config_check", "ga_record_bytes", "ga_workspace_bytes",
@@ -28,6 +29,7 @@ EXPORTED = (
     "ga_curation_sites", "ga_mrca_bounds_noalloc", "ga_batch_create", "ga_batch_add",
     "ga_batch_remove", "ga_batch_size", "ga_batch_step", "ga_batch_sync",
     "ga_batch_launch_count", "ga_batch_autotune", "ga_batch_class_warps", "ga_batch_destroy",
+    "ga_async_window",
 )
 
 
@@ -96,6 +98,7 @@ def load_library(path=LIB_PATH):
         "ga_batch_autotune": ([vp, u32, C.POINTER(u32)], C.c_int),
         "ga_batch_class_warps": ([vp, u32, C.POINTER(u32), C.POINTER(u32)], C.c_int),
         "ga_batch_destroy": ([vp], C.c_int),
+        "ga_async_window": ([vp, u32], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -119,7 +122,7 @@ def make_config(shape: RunShape, stream=0):
     load_library().ga_config_default(C.byref(cfg))
     for k in ("rows", "cols", "island_size", "tournament_size", "p_ben", "p_del",
               "surface_sites", "differentia_bits", "curation", "seed", "run_id", "model",
-              "effect_scale"):
+              "effect_scale", "mode"):
         setattr(cfg, k, getattr(shape, k))
     cfg.stream = stream or None
     return cfg
@@ -174,6 +177,8 @@ class Run:
         self._h = h
         _check(self.lib.ga_migrate_policy(h, 1 if shape.migrate_every else 0,
                                           max(1, shape.migrate_every)), "ga_migrate_policy")
+        if shape.mode != SYNC:
+            self.async_window(shape.async_window)
 
     # -- lifecycle ------------------------------------------------------------------------
     def close(self):
@@ -200,6 +205,10 @@ class Run:
 
     def migrate_policy(self, per_neighbor, every_k):
         _check(self.lib.ga_migrate_policy(self._h, per_neighbor, every_k), "ga_migrate_policy")
+
+    def async_window(self, window):
+        """Generations each launch runs in the asynchronous modes (1..256)."""
+        _check(self.lib.ga_async_window(self._h, window), "ga_async_window")
 
     def step(self, n_gens):
         _check(self.lib.ga_step(self._h, n_gens), "ga_step")

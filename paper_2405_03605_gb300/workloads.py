@@ -15,6 +15,7 @@ import numpy as np
 
 STEADY, TILTED, HYBRID = 0, 1, 2
 MODEL_TRAIT, MODEL_FITNESS = 0, 1
+SYNC, ASYNC, ASYNC_SEQUENTIAL = 0, 1, 2
 
 
 @dataclass(frozen=True)
@@ -34,6 +35,8 @@ class RunShape:
     generations: int = 1000
     model: int = MODEL_TRAIT
     effect_scale: float = 1.0
+    mode: int = SYNC
+    async_window: int = 16  # generations per launch in the asynchronous modes
 
     @property
     def n_islands(self):
@@ -50,7 +53,8 @@ class RunShape:
 
     def kwargs(self):
         d = asdict(self)
-        d.pop("generations")
+        for k in ("generations", "mode", "async_window"):
+            d.pop(k)
         return d
 
     def with_(self, **kw):

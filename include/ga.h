@@ -57,7 +57,7 @@ extern "C" {
 #define GA_HYBRID 2u /* first S/2 sites steady on even ranks, last S/2 tilted on odd ranks */
 
 #define GA_SYNC 0u  /* synchronous generations: deterministic, bit-exact                 */
-#define GA_ASYNC 1u /* asynchronous migration through per-island mailboxes (Sec. 2 WSE loop):
+#define GA_ASYNC 1u /* asynchronous migration through per-island send buffers (Sec. 2 loop):
                        islands advance without waiting for one another, so results depend on
                        scheduling and agents' counters drift apart                         */
 #define GA_ASYNC_SEQUENTIAL 2u /* the GA_ASYNC step on a reproducible schedule: within each
@@ -105,8 +105,7 @@ int ga_config_check(const ga_config *cfg);
 int ga_record_bytes(const ga_config *cfg, uint32_t *bytes);
 
 /* Bytes of device workspace a run of cfg needs (two population buffers plus a header; in the
-   asynchronous modes also four mailboxes of 16 + record_bytes bytes and four 4-byte
-   sequence marks per island). */
+   asynchronous modes also four send buffers of 16 + record_bytes bytes per island). */
 int ga_workspace_bytes(const ga_config *cfg, size_t *bytes);
 
 /*
@@ -131,26 +130,26 @@ int ga_reset(ga_run *run);
 int ga_migrate_policy(ga_run *run, uint32_t per_neighbor, uint32_t every_k);
 
 /*
- * Asynchronous modes (Sec. 2: the wafer-scale loop posts and collects migrants without
- * waiting).  Each island owns one outgoing mailbox per direction (a sequence word and one
- * record).  On each of its migration generations g (g mod every_k == 0) an island, in this
- * order: (1) for directions N, S, E, W takes the record its neighbour last posted towards
- * it, if the neighbour posted since the island last looked and the mailbox is not being
- * written at that moment (otherwise nothing arrives from that direction); arrivals land in
- * slots chosen by the same partial Fisher-Yates draw as in GA_SYNC, missing arrivals
- * leaving their slot alone; (2) posts a copy of member e_d = (bits 8..15 of word 3 of its
- * slot-d birth draw) * N >> 8 of its population to its mailbox towards d; then (3)
- * reproduces as in GA_SYNC.  Nothing ever waits.  A migrant keeps its counter, so the
- * counters of an island's agents drift apart and each deposit uses the site of the
- * agent's own counter.
+ * Asynchronous modes (Sec. 2: the wafer-scale loop tests completion flags of asynchronous
+ * sends and receives and never waits for them).  Each island owns one send buffer per
+ * direction, holding at most one genome; a send completes when the neighbour takes the
+ * genome out.  On each of its migration generations g (g mod every_k == 0) an island, in
+ * this order: (1) tests all eight flags: which neighbours' buffers facing it are full, which
+ * of its own buffers are empty; (2) for directions N, S, E, W takes the genome out of each
+ * full buffer facing it (the buffer becomes empty) and lands it in the slot chosen by the
+ * partial Fisher-Yates draw of GA_SYNC (missing arrivals leave their slot alone); (3) fills
+ * each of its own buffers found empty with a copy of member e_d = (bits 8..15 of word 3 of
+ * its slot-d birth draw) * N >> 8; then (4) reproduces as in GA_SYNC.  Nothing ever waits.
+ * A migrant keeps its counter, so counters drift apart and each deposit uses the site of
+ * the agent's own counter.
  *
  * A launch runs `window` generations of every island (all islands start it at the same
  * generation); neighbours that run in the same launch exchange migrants at most about a
  * window apart.  GA_ASYNC_SEQUENTIAL runs each window island by island in index order: a
  * reproducible schedule the CPU model follows exactly.  window in [1, GA_ASYNC_MAX_WINDOW];
- * the default after ga_create is 16.  Mailboxes and sequence marks are cleared by
- * ga_create, ga_reset and ga_load.  Errors: GA_EINVAL (window out of range),
- * GA_ESTATE (run not in an asynchronous mode).
+ * the default after ga_create is 16.  Send buffers are emptied by ga_create, ga_reset and
+ * ga_load.  Errors: GA_EINVAL (window out of range), GA_ESTATE (run not in an asynchronous
+ * mode).
  */
 int ga_async_window(ga_run *run, uint32_t window);
 

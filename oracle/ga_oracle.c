@@ -291,14 +291,12 @@ typedef struct {
     int32_t *trait2;
     uint32_t *counter2;
     uint32_t *surface2;
-    /* asynchronous mode: per island and direction, the outgoing mailbox (sequence number and
-       one agent) and the last sequence number taken from that neighbour; allocated on first
-       use, all zero = nothing posted, nothing taken */
-    uint32_t *mail_seq;
+    /* asynchronous mode: per island and direction, the send buffer towards that neighbour
+       (full flag and one agent); allocated on first use, all zero = every buffer empty */
+    uint32_t *mail_full;
     int32_t *mail_trait;
     uint32_t *mail_counter;
     uint32_t *mail_surface;
-    uint32_t *seen;
     /* lineage tracking (tests only; off unless orc_track_lineage was called): every agent
        carries the id of the birth that made it, g * n_agents + slot (-1: founder); event_parent
        maps a birth to its parent's birth, event_depth to the child's counter */
@@ -351,11 +349,10 @@ void orc_destroy(orc_state *st)
     free(st->trait2);
     free(st->counter2);
     free(st->surface2);
-    free(st->mail_seq);
+    free(st->mail_full);
     free(st->mail_trait);
     free(st->mail_counter);
     free(st->mail_surface);
-    free(st->seen);
     free(st->tag);
     free(st->tag2);
     free(st->mail_tag);
@@ -632,50 +629,53 @@ void orc_step(orc_state *st, uint32_t n_gens)
 
 static int async_alloc(orc_state *st)
 {
-    if (st->mail_seq) return 0;
+    if (st->mail_full) return 0;
     const size_t boxes = (size_t)st->n_islands * 4;
-    st->mail_seq = (uint32_t *)calloc(boxes, sizeof(uint32_t));
+    st->mail_full = (uint32_t *)calloc(boxes, sizeof(uint32_t));
     st->mail_trait = (int32_t *)calloc(boxes, sizeof(int32_t));
     st->mail_counter = (uint32_t *)calloc(boxes, sizeof(uint32_t));
     st->mail_surface = (uint32_t *)calloc(boxes * st->words, sizeof(uint32_t));
-    st->seen = (uint32_t *)calloc(boxes, sizeof(uint32_t));
-    if (!st->mail_seq || !st->mail_trait || !st->mail_counter || !st->mail_surface || !st->seen)
-        return -2;
+    if (!st->mail_full || !st->mail_trait || !st->mail_counter || !st->mail_surface) return -2;
     return 0;
 }
 
 static void async_clear(orc_state *st)
 {
-    if (!st->mail_seq) return;
+    if (!st->mail_full) return;
     const size_t boxes = (size_t)st->n_islands * 4;
-    memset(st->mail_seq, 0, boxes * sizeof(uint32_t));
+    memset(st->mail_full, 0, boxes * sizeof(uint32_t));
     memset(st->mail_trait, 0, boxes * sizeof(int32_t));
     memset(st->mail_counter, 0, boxes * sizeof(uint32_t));
     memset(st->mail_surface, 0, boxes * st->words * sizeof(uint32_t));
-    memset(st->seen, 0, boxes * sizeof(uint32_t));
 }
 
 /*
- * Migration step of island `isl` at its generation g, asynchronous reading:
- *   1. collect: for d = N, S, E, W the neighbour nb(d)'s mailbox facing isl (its direction
- *      opposite to d) is taken when it holds a post (sequence > 0) other than the last one
- *      isl took from d; the four draws of the synchronous mode place the arrivals: a partial
- *      Fisher-Yates shuffle over all four directions in order (the swap happens whether or
- *      not direction d delivers) and arrival d, if any, replaces the member in position d;
- *   2. post: for each d a copy of member e_d = (bits 8..15 of word 3 of slot d's draw) * N
- *      >> 8 of the island as it stands after step 1 goes to isl's mailbox towards d, whose
- *      sequence number grows by 2.
+ * Migration step of island `isl` at its generation g (Sec. 2: the loop first tests every
+ * completion flag, then copies in what arrived, then refills the send buffers whose send
+ * completed).  Reading used here: each island has one send buffer per direction holding at
+ * most one genome; a send completes when the neighbour takes the genome out.
+ *   1. test: R_d = the buffer of neighbour nb(d) facing isl (nb(d)'s direction opposite to
+ *      d) is full; E_d = isl's own buffer towards d is empty -- all eight tested first;
+ *   2. collect: for d = N, S, E, W in order, the partial Fisher-Yates draw of the synchronous
+ *      mode swaps position d with r_d (whether or not anything arrives); if R_d, the genome
+ *      is taken out of the buffer (which becomes empty) and replaces the member in position d;
+ *   3. refill: for each d with E_d, a copy of member e_d = (bits 8..15 of word 3 of slot d's
+ *      draw) * N >> 8 of the island as it stands after step 2 fills isl's buffer towards d.
  * arrivals (optional, 4 per island) counts deliveries per direction.
  */
 static void async_migrate_island(orc_state *st, uint32_t isl, uint32_t g, uint64_t *arrivals)
 {
     const orc_config *c = &st->cfg;
     const uint32_t N = c->island_size, words = st->words;
-    uint32_t w3[4];
+    uint32_t w3[4], in_box[4];
+    int full_in[4], empty_out[4];
     for (uint32_t d = 0; d < 4; ++d) {
         uint32_t w[4];
         draw(c->seed, g, isl, d, ORC_PURPOSE_BIRTH, c->run_id, w);
         w3[d] = w[3];
+        in_box[d] = neighbour(c, isl, (int)d) * 4 + (d ^ 1u);
+        full_in[d] = st->mail_full[in_box[d]] != 0;
+        empty_out[d] = st->mail_full[isl * 4 + d] == 0;
     }
     uint32_t perm[256];
     for (uint32_t j = 0; j < N; ++j) perm[j] = j;
@@ -684,19 +684,18 @@ static void async_migrate_island(orc_state *st, uint32_t isl, uint32_t g, uint64
         uint32_t tmp = perm[d];
         perm[d] = perm[r];
         perm[r] = tmp;
-        const uint32_t box = neighbour(c, isl, (int)d) * 4 + (d ^ 1u);
-        const uint32_t seq = st->mail_seq[box];
-        if (seq == 0 || seq == st->seen[isl * 4 + d]) continue;
-        st->seen[isl * 4 + d] = seq;
-        const uint32_t dst = isl * N + perm[d];
+        if (!full_in[d]) continue;
+        const uint32_t box = in_box[d], dst = isl * N + perm[d];
         st->trait[dst] = st->mail_trait[box];
         st->counter[dst] = st->mail_counter[box];
         memcpy(&st->surface[(size_t)dst * words], &st->mail_surface[(size_t)box * words],
                words * sizeof(uint32_t));
         if (tracking(st)) st->tag[dst] = st->mail_tag[box];
+        st->mail_full[box] = 0;
         if (arrivals) arrivals[isl * 4 + d] += 1;
     }
     for (uint32_t d = 0; d < 4; ++d) {
+        if (!empty_out[d]) continue;
         const uint32_t e = (((w3[d] >> 8) & 0xFFu) * N) >> 8;
         const uint32_t src = isl * N + e, box = isl * 4 + d;
         st->mail_trait[box] = st->trait[src];
@@ -704,7 +703,7 @@ static void async_migrate_island(orc_state *st, uint32_t isl, uint32_t g, uint64
         memcpy(&st->mail_surface[(size_t)box * words], &st->surface[(size_t)src * words],
                words * sizeof(uint32_t));
         if (tracking(st)) st->mail_tag[box] = st->tag[src];
-        st->mail_seq[box] += 2;
+        st->mail_full[box] = 1;
     }
 }
 

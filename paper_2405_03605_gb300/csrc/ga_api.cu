@@ -71,7 +71,7 @@ size_t population_bytes(const ga_config *c)
 
 size_t buffer_stride(const ga_config *c) { return align_up(population_bytes(c), 256); }
 
-// Workspace: header, two population buffers, then (asynchronous modes) mailboxes and marks.
+// Workspace: header, two population buffers, then (asynchronous modes) the send buffers.
 size_t workspace_need(const ga_config *c)
 {
     size_t need = ga::kHeaderBytes + 2 * buffer_stride(c);
@@ -79,7 +79,7 @@ size_t workspace_need(const ga_config *c)
     return need;
 }
 
-// Clear the mailboxes and sequence marks (asynchronous modes).
+// Empty every send buffer (asynchronous modes).
 int clear_async_state(ga_run *run)
 {
     if (!run->mail) return GA_OK;
@@ -235,14 +235,8 @@ int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_
     run->pop[1] = base + ga::kHeaderBytes + buffer_stride(cfg);
     run->cur = 0;
     run->mail = nullptr;
-    run->seen = nullptr;
     run->async_window = 16;
-    if (cfg->mode != GA_SYNC) {
-        const size_t mail_bytes = align_up(static_cast<size_t>(run->n_islands) * 4u *
-                                               (16u + run->record_bytes), 256);
-        run->mail = base + ga::kHeaderBytes + 2 * buffer_stride(cfg);
-        run->seen = reinterpret_cast<uint32_t *>(run->mail + mail_bytes);
-    }
+    if (cfg->mode != GA_SYNC) run->mail = base + ga::kHeaderBytes + 2 * buffer_stride(cfg);
     rc = cuda_rc(cudaMemsetAsync(base, 0, ga::kHeaderBytes, run->stream));
     if (rc == GA_OK) rc = clear_async_state(run);
     if (rc == GA_OK) rc = cuda_rc(ga::launch_founder(run, run->pop[0]));

@@ -1,33 +1,35 @@
-// ga_async.cu -- the asynchronous island step: migration through per-island mailboxes.
+// ga_async.cu -- the asynchronous island step: migration through one-genome send buffers.
 //
-// This follows the wafer-scale loop of the paper (Sec. 2) more literally than the
-// synchronous mode: each island owns one outgoing mailbox per cardinal direction; on each
-// migration generation it first takes whatever its neighbours posted since it last looked,
-// landing each arrival in a random slot, then refills its own mailboxes with copies of
-// randomly sampled members, then evaluates, selects, mutates and deposits as usual.  Nothing
-// ever waits: an unchanged or half-written mailbox is skipped, so islands exchange migrants
-// at whatever pace the hardware runs them, and a migrant keeps the counter of its lineage
-// (deposit sites then follow each agent's own counter, as in the synchronous kernels'
-// closed-form branch).
+// This follows the wafer-scale loop of the paper (Sec. 2): each island owns one send buffer
+// per cardinal direction; on each migration generation it first tests every completion
+// flag, then copies in the genomes that arrived (each replacing a random member), then
+// refills the send buffers whose previous genome was taken, with copies of randomly sampled
+// members; then it evaluates, selects, mutates and deposits as usual.  Nothing ever waits: a
+// buffer that is not ready is simply skipped, so islands exchange migrants at whatever pace
+// the hardware runs them, and a migrant keeps the counter of its lineage (deposits then
+// follow each agent's own counter, as in the synchronous kernels' closed-form branch).
 //
-// Mailbox protocol (a sequence lock without waiting): the owner stores seq + 1 (odd: being
-// written), fences, stores the record, fences, stores seq + 2.  A reader loads seq and skips
-// the mailbox when seq is zero (never posted), odd (being written) or equal to the last
-// sequence it took; otherwise it loads the record, fences, re-loads seq and keeps the record
-// only if seq did not move.  Mailbox words are accessed with volatile loads and stores (no
-// stale L1 copies) and __threadfence orders them device-wide.  Sequence words grow by 2 per
-// post and wrap after 2^31 posts of one mailbox.
+// Buffer protocol (single producer, single consumer, PTX memory model at GPU scope): the
+// flag word is 0 (empty) or 1 (full).  The owner writes a genome only into an empty buffer
+// (seen with an acquire load), with relaxed stores, and publishes it by a release store of
+// 1; the neighbour takes a genome only from a full buffer (acquire load), with relaxed
+// loads, and hands the buffer back by a release store of 0.  Each side touches the record
+// only while the flag says the buffer is its own, and the release/acquire pairs order the
+// other side's record accesses before its own, so a record is never read half-written.
+// The owner's release of a new genome is issued at the start of its next generation (or at
+// the end of the launch), by which time the record stores have long completed, so the
+// release costs no wait.
 //
 // Draws: the birth draws of the synchronous mode, keyed by the generation the island is
-// running.  For direction d, word 3 of slot d's draw supplies bits 8..15 to choose the
-// member posted towards d (the sender samples) and bits 16..31 for the landing slot of the
-// arrival from d (the partial Fisher-Yates draw of the synchronous mode; an arrival that did
-// not come leaves its slot as it was).
+// running.  For direction d, word 3 of slot d's draw supplies bits 16..31 for the landing
+// slot of the arrival from d (the partial Fisher-Yates draw of the synchronous mode, the
+// swap made whether or not anything arrives) and bits 8..15 for the member sent towards d.
 //
-// Mapping: one island per warp for N >= 32, 32/N islands per warp below; lane d < 4 of an
-// island polls direction d and owns the island's mailbox towards d.  Every lane runs the
-// window's generations back to back with its agents in registers, as in the synchronous
-// kernels.
+// Mapping: one island per warp for N >= 32, 32/N islands per warp below; island lanes 0..3
+// take from the neighbours (lane d: direction d), lanes 4..7 own the island's send buffers
+// (lane 4 + d: towards d), so the eight flag tests of a generation are issued together.
+// Every lane runs the window's generations back to back with its agents in registers, as in
+// the synchronous kernels.
 #include "ga_device.cuh"
 #include "ga_internal.h"
 #include "ga_island.cuh"
@@ -40,15 +42,38 @@ RunParams run_params(const ga_run *run, const void *src, void *dst, uint32_t g0,
 
 namespace {
 
+// GPU-scope memory-model accesses to the send buffers (global memory, 16-byte aligned).
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint4 ld_relaxed_v4(const uint4 *p)
+{
+    uint4 v;
+    asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_v4(uint4 *p, uint4 v)
+{
+    asm volatile("st.relaxed.gpu.global.v4.u32 [%0], {%1, %2, %3, %4};"
+                 :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
 constexpr int kAsyncThreads = 256;
 constexpr int kAsyncWarps = kAsyncThreads / 32;
 
 struct AsyncArgs {
     RunParams r;
     RoundKeys rk;
-    uint4 *mail;       // [island][4] mailboxes of 1 + Q uint4: sequence word, record
-    uint32_t *seen;    // [island][4] last sequence taken from each direction
-    uint32_t every_k;  // migration on generations g with g mod every_k == 0
+    uint4 *mail;           // [island][4] send buffers of 1 + Q uint4: flag word, record
+    uint32_t every_k;      // migration on generations g with g mod every_k == 0
     uint32_t first, last;  // islands [first, last) run in this launch
 };
 
@@ -59,7 +84,7 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_kernel(const Async
     constexpr int LW = 2 + SW;
     constexpr int RW = (LW + 3) / 4 * 4;
     constexpr int Q = RW / 4;
-    constexpr int MB = 1 + Q;  // mailbox size in uint4
+    constexpr int MB = 1 + Q;  // send buffer size in uint4
     const RunParams &p = a.r;
 
     const uint32_t lane = threadIdx.x & 31u;
@@ -84,58 +109,61 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_kernel(const Async
         }
     }
 
-    // lane d < 4: polls the neighbour in direction d (0 north, 1 south, 2 east, 3 west),
-    // whose mailbox facing this island is the opposite direction d ^ 1, and owns this
-    // island's mailbox towards d
-    const uint32_t d = seg_lane;
-    const bool io_lane = d < 4u;
-    volatile uint32_t *in_seq = nullptr;
-    volatile uint32_t *out_seq = nullptr;
-    uint32_t seen = 0, my_seq = 0;
-    if (io_lane) {
+    // lanes 0..3 take from the neighbour in direction d (0 north, 1 south, 2 east, 3 west),
+    // out of its buffer towards this island (its direction d ^ 1); lanes 4..7 own this
+    // island's buffer towards d = lane - 4
+    const uint32_t d = seg_lane & 3u;
+    const bool taker = seg_lane < 4u;
+    const bool sender = seg_lane >= 4u && seg_lane < 8u;
+    uint4 *box = nullptr;
+    if (taker) {
         const uint32_t y = island / p.cols, x = island - y * p.cols;
         const uint32_t yn = d == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
                           : d == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
         const uint32_t xn = d == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
                           : d == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
-        const uint32_t from = yn * p.cols + xn;
-        in_seq = reinterpret_cast<volatile uint32_t *>(
-            a.mail + (static_cast<size_t>(from) * 4u + (d ^ 1u)) * MB);
-        out_seq = reinterpret_cast<volatile uint32_t *>(
-            a.mail + (static_cast<size_t>(island) * 4u + d) * MB);
-        seen = a.seen[static_cast<size_t>(island) * 4u + d];
-        my_seq = *out_seq;
+        box = a.mail + (static_cast<size_t>(yn * p.cols + xn) * 4u + (d ^ 1u)) * MB;
+    } else if (sender) {
+        box = a.mail + (static_cast<size_t>(island) * 4u + d) * MB;
     }
+    uint32_t *const flag = reinterpret_cast<uint32_t *>(box);
+    bool pending = false;  // sender: a genome written, its release not yet issued
 
     for (uint32_t it = 0; it < p.n_gens; ++it) {
         const uint32_t g = p.g0 + it;
         uint4 w[A];
         birth_draws<N>(w, p, a.rk, g, island, seg_lane);
+        if (pending) {
+            st_release(flag, 1u);
+            pending = false;
+        }
 
         if (p.migrate && g % a.every_k == 0u) {
-            // 1. collect: lane d takes its neighbour's latest post, if new and not torn
+            // 1. test all eight flags (after this warp's earlier buffer accesses: an island
+            // can be its own neighbour)
+            __syncwarp(mask);
+            const uint32_t f = (taker || sender) ? ld_acquire(flag) : 0u;
+            __syncwarp(mask);  // every test precedes every take (an island can feed itself)
+            // 2. collect
             uint32_t imm[LW];
 #pragma unroll
             for (int k = 0; k < LW; ++k) imm[k] = 0u;
-            bool arrived = false;
-            if (io_lane) {
-                const uint32_t s1 = *in_seq;
-                if (s1 != 0u && (s1 & 1u) == 0u && s1 != seen) {
-                    __threadfence();
-                    const volatile uint32_t *body = in_seq + 4;
+            const bool arrived = taker && f != 0u;
+            if (arrived) {
 #pragma unroll
-                    for (int k = 0; k < LW; ++k) imm[k] = body[k];
-                    __threadfence();
-                    if (*in_seq == s1) {
-                        arrived = true;
-                        seen = s1;
-                    }
+                for (int q = 0; q < Q; ++q) {
+                    const uint4 xq = ld_relaxed_v4(box + 1 + q);
+                    const uint32_t w4[4] = {xq.x, xq.y, xq.z, xq.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (4 * q + k < LW) imm[4 * q + k] = w4[k];
                 }
+                st_release(flag, 0u);  // the buffer goes back to its owner
             }
             // landing slots: partial Fisher-Yates over [0, N) in direction order (entry e:
             // "position r[e] now holds value v[e]", later entries winning)
-            const uint32_t u = w[0].w;  // word 3 of this lane's slot-seg_lane draw
-            const uint32_t r_own = (d & 3u) + (((u >> 16) * static_cast<uint32_t>(N - (d & 3u))) >> 16);
+            const uint32_t u = __shfl_sync(mask, w[0].w, static_cast<int>(d), SEG);  // slot d's draw
+            const uint32_t r_own = d + (((u >> 16) * static_cast<uint32_t>(N - d)) >> 16);
             uint32_t r[4];
 #pragma unroll
             for (int dd = 0; dd < 4; ++dd) r[dd] = __shfl_sync(mask, r_own, dd, SEG);
@@ -168,7 +196,8 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_kernel(const Async
                     }
                 }
             }
-            // 2. post: lane d copies member e_d of the island (after the arrivals landed)
+            // 3. refill: sender lane 4 + d copies member e_d of the island as it now stands
+            // into an empty buffer; the release follows at the next generation
             const uint32_t e = (((u >> 8) & 0xFFu) * N) >> 8;
             uint32_t out[LW];
 #pragma unroll
@@ -185,23 +214,23 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_kernel(const Async
                     out[k] = val;
                 }
             }
-            if (io_lane) {
-                *out_seq = my_seq + 1u;
-                __threadfence();
-                volatile uint32_t *body = out_seq + 4;
+            if (sender && f == 0u) {
 #pragma unroll
-                for (int k = 0; k < LW; ++k) body[k] = out[k];
-                __threadfence();
-                my_seq += 2u;
-                *out_seq = my_seq;
+                for (int q = 0; q < Q; ++q) {
+                    uint32_t w4[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) w4[k] = (4 * q + k < LW) ? out[4 * q + k] : 0u;
+                    st_relaxed_v4(box + 1 + q, make_uint4(w4[0], w4[1], w4[2], w4[3]));
+                }
+                pending = true;
             }
         }
-        // 3. evaluation, selection, mutation, deposit
+        // 4. evaluation, selection, mutation, deposit
         reproduce<N, SW, 0, MODEL>(rec, w, p, a.rk, island, seg_lane, mask, g,
                                    __ldg(&p.gen_sites[it]));
     }
+    if (pending) st_release(flag, 1u);
 
-    if (io_lane) a.seen[static_cast<size_t>(island) * 4u + d] = seen;
 #pragma unroll
     for (int ag = 0; ag < A; ++ag) {
         const size_t agent = static_cast<size_t>(island) * N + seg_lane + 32u * ag;
@@ -237,8 +266,6 @@ AsyncKernel pick_async(uint32_t island_size, uint32_t surface_words, uint32_t mo
     }
 }
 
-size_t align256(size_t x) { return (x + 255u) / 256u * 256u; }
-
 }  // namespace
 
 bool async_supported(uint32_t island_size, uint32_t surface_words, uint32_t model)
@@ -246,11 +273,11 @@ bool async_supported(uint32_t island_size, uint32_t surface_words, uint32_t mode
     return pick_async(island_size, surface_words, model) != nullptr;
 }
 
-// Mailboxes ([island][4] of 16 + record_bytes bytes), then sequence marks ([island][4] uint32).
+// Send buffers: [island][4] of 16 + record_bytes bytes (flag word padded to 16 bytes, record).
 size_t async_state_bytes(uint32_t n_islands, uint32_t record_bytes)
 {
-    return align256(static_cast<size_t>(n_islands) * 4u * (16u + record_bytes)) +
-           align256(static_cast<size_t>(n_islands) * 16u);
+    const size_t bytes = static_cast<size_t>(n_islands) * 4u * (16u + record_bytes);
+    return (bytes + 255u) / 256u * 256u;
 }
 
 cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_t g0,
@@ -264,7 +291,6 @@ cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_
     a.rk = round_keys(Key{static_cast<uint32_t>(run->cfg.seed),
                           static_cast<uint32_t>(run->cfg.seed >> 32)});
     a.mail = reinterpret_cast<uint4 *>(run->mail);
-    a.seen = run->seen;
     a.every_k = run->every_k;
     a.first = first;
     a.last = last;
@@ -280,7 +306,7 @@ cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_
 // site-table chunks); GA_ASYNC runs every island in one launch per window,
 // GA_ASYNC_SEQUENTIAL one launch per island in index order.  The population is
 // double-buffered per window: every island reads its records from the current buffer and
-// writes them to the other, while mailboxes and sequence marks persist in the workspace.
+// writes them to the other, while the send buffers persist in the workspace.
 int async_step(ga_run *run, uint32_t n_gens, cudaStream_t stream)
 {
     if (run->generation + n_gens > 0xFFFFFFFFull) return GA_EINVAL;

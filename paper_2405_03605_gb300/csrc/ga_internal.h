@@ -30,8 +30,7 @@ struct ga_run {
     uint8_t *pop[2];     // double-buffered population
     int cur;             // index of the current population buffer
     // asynchronous modes only (null otherwise)
-    uint8_t *mail;       // [island][direction] mailboxes: 16-byte sequence word, record
-    uint32_t *seen;      // [island][direction] last sequence taken from that neighbour
+    uint8_t *mail;       // [island][direction] send buffers: 16-byte flag word, record
     uint32_t async_window;
 };
 

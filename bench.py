@@ -55,6 +55,8 @@ def parse_args():
     p.add_argument("--paper-treatments", action="store_true")
     p.add_argument("--treatment-gens", type=int, default=10000)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-async", action="store_true")
+    p.add_argument("--async-gens", type=int, default=2000)
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -340,6 +342,7 @@ def run_ours(args, rank, world, local):
     served = measure_serve(args) if args.serve and rank == 0 else None
     variants = measure_variants(args) if args.variants and rank == 0 else None
     treatments = measure_treatments(args) if args.paper_treatments and rank == 0 else None
+    asynchronous = measure_async(args) if not args.no_async and rank == 0 else None
 
     for r in runs:
         r.close()
@@ -371,6 +374,7 @@ def run_ours(args, rank, world, local):
         **({"serving": served} if served is not None else {}),
         **({"variants": variants} if variants is not None else {}),
         **({"paper_treatments": treatments} if treatments is not None else {}),
+        **({"async": asynchronous} if asynchronous is not None else {}),
         "gpu_launches": launches,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -519,6 +523,57 @@ def measure_treatments(args):
         out[name] = {"agent_gens_per_s": sh.n_agents * gens / (ms / 1000.0),
                      "mean_mrca_depth": depth, "mean_fitness": mean_fit}
         r.close()
+    return out
+
+
+def measure_async(args):
+    """The asynchronous mode (send buffers, Sec. 2 loop) on the 512x1024x32 grid: each
+    treatment from founders for --async-gens generations at window 1 (neighbours at most a
+    generation apart) and window 16 (islands kept in registers 16 generations per launch),
+    then mixed-counter MRCA bounds over 4,096 sampled agents.  Reports agent-generations/s,
+    the median counter over the generation (1 when no lineage outruns the schedule), the
+    mean MRCA depth min(Ta, Tb) - hi and the MRCA time."""
+    import numpy as np
+    import torch
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import (ASYNC, PAPER_ADAPTIVE, PAPER_PURIFYING,
+                                                  sample_agent_ids)
+
+    gens = args.async_gens
+    stream = torch.cuda.Stream()
+    n = 4096
+    ids_h = sample_agent_ids(args.rows * args.cols * 32, n, seed=9)
+    with torch.cuda.stream(stream):
+        ids = torch.from_numpy(ids_h.view(np.int32)).cuda()
+        iu = torch.triu_indices(n, n, 1, device="cuda")
+    out = {"generations": gens, "workload": f"{args.rows}x{args.cols} islands x 32 agents"}
+    base = {"adaptive": PAPER_ADAPTIVE.with_(rows=args.rows, cols=args.cols),
+            "purifying": PAPER_PURIFYING.with_(rows=args.rows, cols=args.cols)}
+    for window in (1, 16):
+        for name, sh in base.items():
+            sh = sh.with_(mode=ASYNC, async_window=window)
+            r = ga.Run(sh, stream=stream)
+            r.step(window)  # warm-up launch
+            r.reset()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            r.step(gens)
+            e1.record(stream)
+            lo, hi = r.mrca_bounds_device(ids)
+            e2.record(stream)
+            r.sync()
+            with torch.cuda.stream(stream):
+                cnt = r.snapshot_device()[:, 4:8].contiguous().view(torch.int32).view(-1)
+                c = cnt[ids.long()].to(torch.int64)
+                T = torch.minimum(c[iu[0]], c[iu[1]])
+                depth = (T - hi.to(torch.int64)).double().mean().item()
+                med = cnt.to(torch.int64).median().item()
+            stream.synchronize()
+            out[f"window{window}_{name}"] = {
+                "agent_gens_per_s": sh.n_agents * gens / (e0.elapsed_time(e1) / 1000.0),
+                "median_counter_over_generation": med / gens,
+                "mean_mrca_depth": depth, "mrca_ms": e1.elapsed_time(e2)}
+            r.close()
     return out
 
 

@@ -134,20 +134,24 @@ int ga_migrate_policy(ga_run *run, uint32_t per_neighbor, uint32_t every_k);
  * sends and receives and never waits for them).  Each island owns one send buffer per
  * direction, holding at most one genome; a send completes when the neighbour takes the
  * genome out.  On each of its migration generations g (g mod every_k == 0) an island, in
- * this order: (1) tests all eight flags: which neighbours' buffers facing it are full, which
- * of its own buffers are empty; (2) for directions N, S, E, W takes the genome out of each
- * full buffer facing it (the buffer becomes empty) and lands it in the slot chosen by the
- * partial Fisher-Yates draw of GA_SYNC (missing arrivals leave their slot alone); (3) fills
- * each of its own buffers found empty with a copy of member e_d = (bits 8..15 of word 3 of
- * its slot-d birth draw) * N >> 8; then (4) reproduces as in GA_SYNC.  Nothing ever waits.
+ * this order: (1) for directions N, S, E, W takes the genome out of each full buffer facing
+ * it (the buffer becomes empty) and lands it in the slot chosen by the partial Fisher-Yates
+ * draw of GA_SYNC (missing arrivals leave their slot alone); (2) fills each of its own
+ * buffers that is empty with a copy of member e_d = (bits 8..15 of word 3 of its slot-d
+ * birth draw) * N >> 8, unless that member's counter is 2^32 - 1 (never sent: that record
+ * value marks an empty buffer); then (3) reproduces as in GA_SYNC.  Nothing ever waits.
  * A migrant keeps its counter, so counters drift apart and each deposit uses the site of
  * the agent's own counter.
  *
  * A launch runs `window` generations of every island (all islands start it at the same
- * generation); neighbours that run in the same launch exchange migrants at most about a
- * window apart.  GA_ASYNC_SEQUENTIAL runs each window island by island in index order: a
- * reproducible schedule the CPU model follows exactly.  window in [1, GA_ASYNC_MAX_WINDOW];
- * the default after ga_create is 16.  Send buffers are emptied by ga_create, ga_reset and
+ * generation).  With window 1 no island gets more than a generation ahead of another, as
+ * when processors run side by side.  Larger windows keep each island in registers for
+ * longer (faster), but a launch whose blocks run in many waves lets islands of late blocks
+ * start a window after early ones have finished it; a lineage that keeps migrating towards
+ * later blocks is then born in each of them and its counter runs ahead of the generation
+ * -- under beneficial mutation such lineages are fitter and take over.  GA_ASYNC_SEQUENTIAL
+ * runs each window island by island in index order: a reproducible schedule the CPU model
+ * follows exactly.  window in [1, GA_ASYNC_MAX_WINDOW]; the default after ga_create is 1.  Send buffers are emptied by ga_create, ga_reset and
  * ga_load.  Errors: GA_EINVAL (window out of range), GA_ESTATE (run not in an asynchronous
  * mode).
  */

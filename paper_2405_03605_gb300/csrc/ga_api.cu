@@ -83,9 +83,7 @@ size_t workspace_need(const ga_config *c)
 int clear_async_state(ga_run *run)
 {
     if (!run->mail) return GA_OK;
-    const cudaError_t e = cudaMemsetAsync(
-        run->mail, 0, ga::async_state_bytes(run->n_islands, run->record_bytes), run->stream);
-    return e == cudaSuccess ? GA_OK : GA_ECUDA;
+    return ga::async_clear(run, run->stream) == cudaSuccess ? GA_OK : GA_ECUDA;
 }
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? GA_OK : GA_ECUDA; }
@@ -235,7 +233,7 @@ int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_
     run->pop[1] = base + ga::kHeaderBytes + buffer_stride(cfg);
     run->cur = 0;
     run->mail = nullptr;
-    run->async_window = 16;
+    run->async_window = 1;
     if (cfg->mode != GA_SYNC) run->mail = base + ga::kHeaderBytes + 2 * buffer_stride(cfg);
     rc = cuda_rc(cudaMemsetAsync(base, 0, ga::kHeaderBytes, run->stream));
     if (rc == GA_OK) rc = clear_async_state(run);

@@ -1,24 +1,41 @@
 // ga_async.cu -- the asynchronous island step: migration through one-genome send buffers.
 //
 // This follows the wafer-scale loop of the paper (Sec. 2): each island owns one send buffer
-// per cardinal direction; on each migration generation it first tests every completion
-// flag, then copies in the genomes that arrived (each replacing a random member), then
-// refills the send buffers whose previous genome was taken, with copies of randomly sampled
-// members; then it evaluates, selects, mutates and deposits as usual.  Nothing ever waits: a
-// buffer that is not ready is simply skipped, so islands exchange migrants at whatever pace
-// the hardware runs them, and a migrant keeps the counter of its lineage (deposits then
-// follow each agent's own counter, as in the synchronous kernels' closed-form branch).
+// per cardinal direction; on each migration generation it copies in the genomes whose
+// receive completed (each replacing a random member), then refills the send buffers whose
+// send completed -- those whose genome the neighbour has taken -- with copies of randomly
+// sampled members; then it evaluates, selects, mutates and deposits as usual.  Nothing ever
+// waits: a buffer that is not ready is simply skipped, so islands exchange migrants at
+// whatever pace the hardware runs them, and a migrant keeps the counter of its lineage
+// (deposits then follow each agent's own counter, as in the synchronous kernels'
+// closed-form branch).  A genome whose counter is 2^32 - 1 is never sent (that record value
+// marks an empty buffer).
 //
-// Buffer protocol (single producer, single consumer, PTX memory model at GPU scope): the
-// flag word is 0 (empty) or 1 (full).  The owner writes a genome only into an empty buffer
-// (seen with an acquire load), with relaxed stores, and publishes it by a release store of
-// 1; the neighbour takes a genome only from a full buffer (acquire load), with relaxed
-// loads, and hands the buffer back by a release store of 0.  Each side touches the record
-// only while the flag says the buffer is its own, and the release/acquire pairs order the
-// other side's record accesses before its own, so a record is never read half-written.
-// The owner's release of a new genome is issued at the start of its next generation (or at
-// the end of the launch), by which time the record stores have long completed, so the
-// release costs no wait.
+// Two handoff protocols, both single producer / single consumer and wait-free:
+//
+//  * 16-byte records (the paper's 128-bit genome): the buffer is the record itself, all
+//    ones when empty.  The neighbour takes with one 128-bit atomic exchange (leaving all
+//    ones) and the owner refills with one 128-bit compare-and-swap against all ones, so a
+//    record moves in a single atomic access and is never seen half-written.  The take for a
+//    generation is issued right after the previous generation's buffer step and its result
+//    is used a generation later, so its latency hides behind reproduction; the refill's
+//    result is never needed, so nothing waits on it.
+//
+//  * 32- and 48-byte records: a flag word (0 empty, 1 full) beside the record, in the PTX
+//    memory model at GPU scope.  The owner writes a genome only into an empty buffer, with
+//    relaxed stores, and publishes it by a release store of 1 at the start of its next
+//    generation (or the end of the launch), when the record stores have long completed; the
+//    neighbour takes a genome only from a full buffer, with relaxed loads, and hands the
+//    buffer back by a release store of 0.  Flag tests are relaxed loads issued right after
+//    the previous generation's buffer step and followed, before the record is touched, by
+//    an acq_rel fence that makes them acquires; a buffer whose publication is still due
+//    counts as full.
+//
+// On tori with one row or one column an island is its own neighbour, so its own lanes sit
+// on both sides of a buffer: there the takes are made at the start of the generation and the
+// refills after them, between warp barriers, and publication is immediate.  On the
+// sequential schedule (one island per launch) every variant gives the same result as the
+// oracle's model: take, land, then refill what is empty.
 //
 // Draws: the birth draws of the synchronous mode, keyed by the generation the island is
 // running.  For direction d, word 3 of slot d's draw supplies bits 16..31 for the landing
@@ -27,9 +44,8 @@
 //
 // Mapping: one island per warp for N >= 32, 32/N islands per warp below; island lanes 0..3
 // take from the neighbours (lane d: direction d), lanes 4..7 own the island's send buffers
-// (lane 4 + d: towards d), so the eight flag tests of a generation are issued together.
-// Every lane runs the window's generations back to back with its agents in registers, as in
-// the synchronous kernels.
+// (lane 4 + d: towards d).  Every lane runs the window's generations back to back with its
+// agents in registers, as in the synchronous kernels.
 #include "ga_device.cuh"
 #include "ga_internal.h"
 #include "ga_island.cuh"
@@ -42,13 +58,16 @@ RunParams run_params(const ga_run *run, const void *src, void *dst, uint32_t g0,
 
 namespace {
 
+constexpr uint32_t kNeverSent = 0xFFFFFFFFu;  // counter value of the empty-buffer record
+
 // GPU-scope memory-model accesses to the send buffers (global memory, 16-byte aligned).
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
 {
     uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ uint4 ld_relaxed_v4(const uint4 *p)
 {
     uint4 v;
@@ -66,25 +85,73 @@ __device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long pack64(uint32_t lo, uint32_t hi)
+{
+    return static_cast<unsigned long long>(lo) | (static_cast<unsigned long long>(hi) << 32);
+}
+
+// 128-bit atomic exchange: the record at p is replaced by all ones and returned.
+__device__ __forceinline__ uint4 take128(uint4 *p)
+{
+    unsigned long long lo, hi;
+    const unsigned long long ones = ~0ull;
+    asm volatile("{\n\t.reg .b128 nv, ov;\n\t"
+                 "mov.b128 nv, {%2, %3};\n\t"
+                 "atom.relaxed.gpu.global.exch.b128 ov, [%4], nv;\n\t"
+                 "mov.b128 {%0, %1}, ov;\n\t}"
+                 : "=l"(lo), "=l"(hi) : "l"(ones), "l"(ones), "l"(p) : "memory");
+    return make_uint4(static_cast<uint32_t>(lo), static_cast<uint32_t>(lo >> 32),
+                      static_cast<uint32_t>(hi), static_cast<uint32_t>(hi >> 32));
+}
+
+// 128-bit compare-and-swap: the record v is stored at p if p holds all ones (empty).  The
+// outcome is not needed, so the caller never waits for it.
+__device__ __forceinline__ void refill128(uint4 *p, const uint32_t (&v)[4])
+{
+    unsigned long long lo, hi;
+    const unsigned long long ones = ~0ull;
+    asm volatile("{\n\t.reg .b128 cv, nv, ov;\n\t"
+                 "mov.b128 cv, {%2, %3};\n\t"
+                 "mov.b128 nv, {%4, %5};\n\t"
+                 "atom.relaxed.gpu.global.cas.b128 ov, [%6], cv, nv;\n\t"
+                 "mov.b128 {%0, %1}, ov;\n\t}"
+                 : "=l"(lo), "=l"(hi)
+                 : "l"(ones), "l"(ones), "l"(pack64(v[0], v[1])), "l"(pack64(v[2], v[3])), "l"(p)
+                 : "memory");
+}
+
 constexpr int kAsyncThreads = 256;
 constexpr int kAsyncWarps = kAsyncThreads / 32;
 
 struct AsyncArgs {
     RunParams r;
     RoundKeys rk;
-    uint4 *mail;           // [island][4] send buffers of 1 + Q uint4: flag word, record
+    uint4 *mail;           // [island][4] send buffers (16-byte records: the record itself;
+                           // otherwise 1 + Q uint4: flag word, record)
     uint32_t every_k;      // migration on generations g with g mod every_k == 0
     uint32_t first, last;  // islands [first, last) run in this launch
 };
 
-template <int N, int SW, int MODEL>
-__global__ void __launch_bounds__(kAsyncThreads) island_async_kernel(const AsyncArgs a)
+// Send-buffer size in uint4 for a record of Q uint4.
+__host__ __device__ constexpr int box_words(int Q) { return Q == 1 ? 1 : 1 + Q; }
+
+// Resident blocks per SM asked of the compiler: the buffer steps are latency-bound, so
+// occupancy pays; six blocks (40 registers) fit the 16-byte-record kernels of N <= 32
+// without spilling, the others keep their registers.
+template <int N, int SW>
+constexpr int async_min_blocks() { return SW <= 2 && N <= 32 ? 6 : 1; }
+
+// TS: the tournament size when fixed at compile time (0: read from the run).
+template <int N, int SW, int TS, int MODEL>
+__global__ void __launch_bounds__(kAsyncThreads, (async_min_blocks<N, SW>()))
+island_async_kernel(const AsyncArgs a)
 {
     constexpr int A = Shape<N>::A, P = Shape<N>::P, SEG = Shape<N>::SEG;
     constexpr int LW = 2 + SW;
     constexpr int RW = (LW + 3) / 4 * 4;
     constexpr int Q = RW / 4;
-    constexpr int MB = 1 + Q;  // send buffer size in uint4
+    constexpr bool kAtomic = Q == 1;  // the whole record in one 128-bit atomic
+    constexpr int MB = box_words(Q);
     const RunParams &p = a.r;
 
     const uint32_t lane = threadIdx.x & 31u;
@@ -126,39 +193,66 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_kernel(const Async
     } else if (sender) {
         box = a.mail + (static_cast<size_t>(island) * 4u + d) * MB;
     }
-    uint32_t *const flag = reinterpret_cast<uint32_t *>(box);
-    bool pending = false;  // sender: a genome written, its release not yet issued
+    uint32_t *const flag = reinterpret_cast<uint32_t *>(box);  // flag protocol only
+    const bool early = p.rows > 1u && p.cols > 1u;  // no island is its own neighbour
+    uint4 got = make_uint4(~0u, ~0u, ~0u, ~0u);     // atomic protocol: the taken record
+    uint32_t f = 0;                                 // flag protocol: the tested flag
+    bool pending = false;                           // flag protocol: publication due
+
+    // Take (atomic protocol) or test (flag protocol) ahead of a migration generation's
+    // buffer step.
+    auto prepare = [&]() {
+        if constexpr (kAtomic) {
+            if (taker) got = take128(box);
+        } else {
+            if (taker || sender) f = pending ? 1u : ld_relaxed(flag);
+        }
+    };
+    if (early && p.migrate && p.g0 % a.every_k == 0u) prepare();
 
     for (uint32_t it = 0; it < p.n_gens; ++it) {
         const uint32_t g = p.g0 + it;
         uint4 w[A];
         birth_draws<N>(w, p, a.rk, g, island, seg_lane);
-        if (pending) {
-            st_release(flag, 1u);
-            pending = false;
+        const bool mig = p.migrate && g % a.every_k == 0u;
+        if (mig && !early) {
+            __syncwarp(mask);  // after the previous generation's refills by this warp
+            prepare();
+        }
+        if constexpr (!kAtomic) {
+            if (mig) fence_acq_rel();  // the flag tests act as acquire loads
+            if (pending) {             // sends started in the previous generation complete
+                st_release(flag, 1u);
+                pending = false;
+            }
         }
 
-        if (p.migrate && g % a.every_k == 0u) {
-            // 1. test all eight flags (after this warp's earlier buffer accesses: an island
-            // can be its own neighbour)
-            __syncwarp(mask);
-            const uint32_t f = (taker || sender) ? ld_acquire(flag) : 0u;
-            __syncwarp(mask);  // every test precedes every take (an island can feed itself)
-            // 2. collect
+        if (mig) {
+            // 1. collect
             uint32_t imm[LW];
 #pragma unroll
             for (int k = 0; k < LW; ++k) imm[k] = 0u;
-            const bool arrived = taker && f != 0u;
-            if (arrived) {
+            bool arrived;
+            if constexpr (kAtomic) {
+                arrived = taker && got.y != kNeverSent;
+                if (arrived) {
+                    const uint32_t g4[4] = {got.x, got.y, got.z, got.w};
 #pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const uint4 xq = ld_relaxed_v4(box + 1 + q);
-                    const uint32_t w4[4] = {xq.x, xq.y, xq.z, xq.w};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (4 * q + k < LW) imm[4 * q + k] = w4[k];
+                    for (int k = 0; k < LW; ++k) imm[k] = g4[k];
                 }
-                st_release(flag, 0u);  // the buffer goes back to its owner
+            } else {
+                arrived = taker && f != 0u;
+                if (arrived) {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const uint4 xq = ld_relaxed_v4(box + 1 + q);
+                        const uint32_t w4[4] = {xq.x, xq.y, xq.z, xq.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (4 * q + k < LW) imm[4 * q + k] = w4[k];
+                    }
+                    st_release(flag, 0u);  // the buffer goes back to its owner
+                }
             }
             // landing slots: partial Fisher-Yates over [0, N) in direction order (entry e:
             // "position r[e] now holds value v[e]", later entries winning)
@@ -196,8 +290,8 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_kernel(const Async
                     }
                 }
             }
-            // 3. refill: sender lane 4 + d copies member e_d of the island as it now stands
-            // into an empty buffer; the release follows at the next generation
+            // 2. refill: sender lane 4 + d copies member e_d of the island as it now stands
+            // into its buffer if that is empty
             const uint32_t e = (((u >> 8) & 0xFFu) * N) >> 8;
             uint32_t out[LW];
 #pragma unroll
@@ -214,22 +308,41 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_kernel(const Async
                     out[k] = val;
                 }
             }
-            if (sender && f == 0u) {
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    uint32_t w4[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) w4[k] = (4 * q + k < LW) ? out[4 * q + k] : 0u;
-                    st_relaxed_v4(box + 1 + q, make_uint4(w4[0], w4[1], w4[2], w4[3]));
+            const bool sendable = sender && out[1] != kNeverSent;
+            if (!early) __syncwarp(mask);  // after this generation's takes by this warp
+            if constexpr (kAtomic) {
+                if (sendable) refill128(box, out);
+            } else {
+                bool fill;
+                if (early) {
+                    fill = sendable && f == 0u;
+                } else {
+                    const uint32_t now = sender ? ld_relaxed(flag) : 1u;
+                    fence_acq_rel();
+                    fill = sendable && now == 0u;
                 }
-                pending = true;
+                if (fill) {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        uint32_t w4[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) w4[k] = (4 * q + k < LW) ? out[4 * q + k] : 0u;
+                        st_relaxed_v4(box + 1 + q, make_uint4(w4[0], w4[1], w4[2], w4[3]));
+                    }
+                    if (early) pending = true;
+                    else st_release(flag, 1u);
+                }
             }
         }
-        // 4. evaluation, selection, mutation, deposit
-        reproduce<N, SW, 0, MODEL>(rec, w, p, a.rk, island, seg_lane, mask, g,
-                                   __ldg(&p.gen_sites[it]));
+        // the next generation's take / test, in flight during this generation's reproduction
+        if (early && p.migrate && it + 1u < p.n_gens && (g + 1u) % a.every_k == 0u) prepare();
+        // 3. evaluation, selection, mutation, deposit
+        reproduce<N, SW, TS, MODEL>(rec, w, p, a.rk, island, seg_lane, mask, g,
+                                    __ldg(&p.gen_sites[it]));
     }
-    if (pending) st_release(flag, 1u);
+    if constexpr (!kAtomic) {
+        if (pending) st_release(flag, 1u);
+    }
 
 #pragma unroll
     for (int ag = 0; ag < A; ++ag) {
@@ -246,45 +359,70 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_kernel(const Async
 
 using AsyncKernel = void (*)(AsyncArgs);
 
-template <int N>
+template <int N, int TS>
 AsyncKernel pick_async_n(uint32_t surface_words, uint32_t model)
 {
-    if (model == GA_MODEL_FITNESS) return surface_words <= 2 ? island_async_kernel<N, 2, 1> : nullptr;
-    if (surface_words <= 2) return island_async_kernel<N, 2, 0>;
-    if (surface_words <= 6) return island_async_kernel<N, 6, 0>;
-    if (surface_words <= 8) return island_async_kernel<N, 8, 0>;
+    if (model == GA_MODEL_FITNESS) return surface_words <= 2 ? island_async_kernel<N, 2, TS, 1> : nullptr;
+    if (surface_words <= 2) return island_async_kernel<N, 2, TS, 0>;
+    if (surface_words <= 6) return island_async_kernel<N, 6, TS, 0>;
+    if (surface_words <= 8) return island_async_kernel<N, 8, TS, 0>;
     return nullptr;
 }
 
-AsyncKernel pick_async(uint32_t island_size, uint32_t surface_words, uint32_t model)
+// Tournament size 5 (the paper's) is compiled in; other sizes are read from the run.
+template <int N>
+AsyncKernel pick_async_ts(uint32_t surface_words, uint32_t tsize, uint32_t model)
+{
+    return tsize == 5u ? pick_async_n<N, 5>(surface_words, model)
+                       : pick_async_n<N, 0>(surface_words, model);
+}
+
+AsyncKernel pick_async(uint32_t island_size, uint32_t surface_words, uint32_t tsize, uint32_t model)
 {
     switch (island_size) {
-    case 16: return pick_async_n<16>(surface_words, model);
-    case 32: return pick_async_n<32>(surface_words, model);
-    case 64: return pick_async_n<64>(surface_words, model);
+    case 16: return pick_async_ts<16>(surface_words, tsize, model);
+    case 32: return pick_async_ts<32>(surface_words, tsize, model);
+    case 64: return pick_async_ts<64>(surface_words, tsize, model);
     default: return nullptr;
     }
+}
+
+// 16-byte records travel through 16-byte buffers (all ones when empty); larger records
+// through a 16-byte flag word plus the record (flag 0 when empty).
+bool atomic_buffers(uint32_t record_bytes) { return record_bytes == 16u; }
+
+size_t buffer_bytes(uint32_t record_bytes)
+{
+    return atomic_buffers(record_bytes) ? 16u : 16u + record_bytes;
 }
 
 }  // namespace
 
 bool async_supported(uint32_t island_size, uint32_t surface_words, uint32_t model)
 {
-    return pick_async(island_size, surface_words, model) != nullptr;
+    return pick_async(island_size, surface_words, 1u, model) != nullptr;
 }
 
-// Send buffers: [island][4] of 16 + record_bytes bytes (flag word padded to 16 bytes, record).
+// Send buffers: [island][4] buffers.
 size_t async_state_bytes(uint32_t n_islands, uint32_t record_bytes)
 {
-    const size_t bytes = static_cast<size_t>(n_islands) * 4u * (16u + record_bytes);
+    const size_t bytes = static_cast<size_t>(n_islands) * 4u * buffer_bytes(record_bytes);
     return (bytes + 255u) / 256u * 256u;
+}
+
+// Empty every send buffer.
+cudaError_t async_clear(ga_run *run, cudaStream_t stream)
+{
+    return cudaMemsetAsync(run->mail, atomic_buffers(run->record_bytes) ? 0xFF : 0x00,
+                           async_state_bytes(run->n_islands, run->record_bytes), stream);
 }
 
 cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_t g0,
                                 uint32_t n_gens, uint32_t first, uint32_t last,
                                 cudaStream_t stream)
 {
-    const AsyncKernel k = pick_async(run->cfg.island_size, run->surface_words, run->cfg.model);
+    const AsyncKernel k = pick_async(run->cfg.island_size, run->surface_words,
+                                     run->cfg.tournament_size, run->cfg.model);
     if (!k || first >= last || last > run->n_islands) return cudaErrorInvalidValue;
     AsyncArgs a;
     a.r = run_params(run, src, dst, g0, n_gens, run->per_neighbor != 0);

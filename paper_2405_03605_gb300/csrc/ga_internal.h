@@ -30,7 +30,7 @@ struct ga_run {
     uint8_t *pop[2];     // double-buffered population
     int cur;             // index of the current population buffer
     // asynchronous modes only (null otherwise)
-    uint8_t *mail;       // [island][direction] send buffers: 16-byte flag word, record
+    uint8_t *mail;       // [island][direction] send buffers
     uint32_t async_window;
 };
 
@@ -62,6 +62,8 @@ size_t mrca_scratch_bytes(const ga_run *run, uint32_t n);
 // Asynchronous mode (ga_async.cu).
 bool async_supported(uint32_t island_size, uint32_t surface_words, uint32_t model);
 size_t async_state_bytes(uint32_t n_islands, uint32_t record_bytes);
+// Empty every send buffer of an asynchronous run.
+cudaError_t async_clear(ga_run *run, cudaStream_t stream);
 // Generations [g0, g0 + n_gens) of islands [first, last), reading src and writing dst.
 cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_t g0,
                                 uint32_t n_gens, uint32_t first, uint32_t last,

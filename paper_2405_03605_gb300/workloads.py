@@ -36,7 +36,7 @@ class RunShape:
     model: int = MODEL_TRAIT
     effect_scale: float = 1.0
     mode: int = SYNC
-    async_window: int = 16  # generations per launch in the asynchronous modes
+    async_window: int = 1  # generations per launch in the asynchronous modes
 
     @property
     def n_islands(self):

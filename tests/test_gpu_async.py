@@ -16,7 +16,7 @@ import pytest
 import oracle
 from gpu_util import assert_same, gpu_run, oracle_for
 from paper_2405_03605_gb300.workloads import RunShape, STEADY, TILTED, HYBRID, \
-    SYNC, ASYNC, ASYNC_SEQUENTIAL, MODEL_FITNESS
+    SYNC, ASYNC, ASYNC_SEQUENTIAL, MODEL_FITNESS, sample_agent_ids
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +33,9 @@ def _sequential_both(shape, calls):
 
 
 # drift: the oracle's end state holds agents of different counters (genomes that arrived
-# late survived), so those cases exercise deposits at counters other than the generation
+# late survived), so those cases exercise deposits at counters other than the generation.
+# 16-byte records take the atomic handoff, 32/48-byte ones the flag handoff; tori with one
+# row or column (an island its own neighbour) take the in-generation ordering.
 @pytest.mark.parametrize("rows,cols,N,S,b,policy,window,every,drift", [
     (1, 1, 16, 64, 1, STEADY, 5, 1, True),
     (1, 2, 32, 64, 1, STEADY, 3, 1, True),
@@ -94,7 +96,7 @@ def test_free_running_single_island_matches_oracle(window):
 
 def test_free_running_invariants_and_mrca():
     shape = RunShape(rows=256, cols=64, island_size=32, seed=11, p_ben=0.05, p_del=0.05,
-                     mode=ASYNC, async_window=16)
+                     mode=ASYNC, async_window=16)  # many block waves: counters run ahead
     g = gpu_run(shape)
     g.step(400)
     g.sync()
@@ -109,6 +111,42 @@ def test_free_running_invariants_and_mrca():
     elo, ehi = oracle.mrca_bounds_mixed(rec, ids, shape.curation, shape.surface_sites,
                                         shape.differentia_bits)
     assert np.array_equal(lo, elo) and np.array_equal(hi, ehi)
+
+
+def _mean_depth(g, ids, shape):
+    """Mean over pairs of min(Ta, Tb) - hi: how long ago, at least, two lineages split."""
+    rec = g.snapshot()
+    lo, hi = g.mrca_bounds(ids)
+    c = rec[:, 4:8].copy().view(np.uint32).ravel()[ids].astype(np.int64)
+    T = np.minimum(c[:, None], c[None, :])[np.triu_indices(len(ids), 1)]
+    assert np.all(lo <= hi) and np.all(hi <= T)
+    return float(np.mean(T - hi.astype(np.int64)))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_free_running_counters_and_treatment_contrast(seed):
+    """Window 1 (neighbours at most a generation apart).  Every agent descends, through at
+    least one birth per generation, from an agent or a buffered copy of the previous
+    snapshot, so the smallest counter never falls; |trait| <= counter; and purifying-only
+    runs keep far deeper genealogies than adaptive ones (Sec. 3), measured by the
+    mixed-counter MRCA bounds."""
+    depth = {}
+    for p_ben in (0.01, 0.0):
+        shape = RunShape(rows=8, cols=8, p_ben=p_ben, p_del=0.01, seed=seed,
+                         run_id=int(p_ben > 0), mode=ASYNC, async_window=1)
+        g = gpu_run(shape)
+        low = 0
+        for _ in range(6):
+            g.step(100)
+            g.sync()
+            w = g.snapshot().view(np.uint32).reshape(shape.n_agents, -1)
+            c = w[:, 1].astype(np.int64)
+            assert c.min() >= low and c.min() >= 1
+            assert np.all(np.abs(w[:, 0].view(np.int32).astype(np.int64)) <= c)
+            low = int(c.min())
+        ids = sample_agent_ids(shape.n_agents, 200, seed=seed)
+        depth[p_ben] = _mean_depth(g, ids, shape)
+    assert depth[0.0] > depth[0.01] + 100, depth
 
 
 def _forked_population(n_agents, S, b, policy, t_lo, t_hi, seed):

@@ -208,13 +208,16 @@ island_async_kernel(const AsyncArgs a)
             if (taker || sender) f = pending ? 1u : ld_relaxed(flag);
         }
     };
-    if (early && p.migrate && p.g0 % a.every_k == 0u) prepare();
+    // generations since the last migration generation (g mod every_k), kept incrementally
+    uint32_t phase = p.g0 % a.every_k;
+    if (early && p.migrate && phase == 0u) prepare();
 
     for (uint32_t it = 0; it < p.n_gens; ++it) {
         const uint32_t g = p.g0 + it;
         uint4 w[A];
         birth_draws<N>(w, p, a.rk, g, island, seg_lane);
-        const bool mig = p.migrate && g % a.every_k == 0u;
+        const bool mig = p.migrate && phase == 0u;
+        phase = phase + 1u == a.every_k ? 0u : phase + 1u;  // now (g + 1) mod every_k
         if (mig && !early) {
             __syncwarp(mask);  // after the previous generation's refills by this warp
             prepare();
@@ -335,7 +338,7 @@ island_async_kernel(const AsyncArgs a)
             }
         }
         // the next generation's take / test, in flight during this generation's reproduction
-        if (early && p.migrate && it + 1u < p.n_gens && (g + 1u) % a.every_k == 0u) prepare();
+        if (early && p.migrate && it + 1u < p.n_gens && phase == 0u) prepare();
         // 3. evaluation, selection, mutation, deposit
         reproduce<N, SW, TS, MODEL>(rec, w, p, a.rk, island, seg_lane, mask, g,
                                     __ldg(&p.gen_sites[it]));

@@ -5,10 +5,11 @@
 //   1. rank_kernel   : replay the curation rule over ranks 0..T-1; each site keeps the
 //                      largest rank that landed on it (atomicMax of rank + 1).
 //   2. order_kernel  : sort the occupied sites by rank (one block, S <= 256): r_1 < ... < r_m.
+//      (For T <= 16384 rank_order_kernel does both in one block, the table in shared memory.)
 //   3. pack_kernel   : gather each sampled agent's differentiae in rank order into a bit
 //                      string (differentia i at bits [i*b, i*b + b)), 8 words per agent; one
 //                      warp per agent, one warp OR-reduction per packed word.
-//   4. pair_kernel   : one thread per pair (i, j), j > i; the first set bit of
+//   4. pair_kernel   : one thread per pair (i, j), j > i, in output order; the first set bit of
 //                      packed[i] ^ packed[j] gives the first mismatching rank index i*,
 //                      from which hi = r_{i*} and lo = r_{i*-K} + 1 (0 if i* <= K); with no
 //                      mismatch hi = T, lo = r_{m-K+1} + 1 (0 if m < K).
@@ -25,6 +26,7 @@ namespace {
 
 constexpr uint32_t kPackWords = 8;  // 256-bit rank-ordered strings
 constexpr int kPairThreads = 256;
+constexpr unsigned long long kPairGrid = 152ull * 8ull;  // 8 resident blocks on each of 152 SMs
 
 struct MrcaLayout {
     uint32_t *holder;  // [S]  rank + 1 held by each site (0: none)
@@ -82,6 +84,52 @@ __global__ void order_kernel(const uint32_t *__restrict__ holder, uint32_t *__re
     if (k == 0) meta[0] = static_cast<uint32_t>(m);
 }
 
+// Counters up to kFusedRankMax: the replay and the sort in one block, the site table in
+// shared memory (one launch instead of a memset and two kernels).
+constexpr uint32_t kFusedRankMax = 16384;
+
+__global__ void __launch_bounds__(1024)
+rank_order_kernel(uint32_t *__restrict__ order, uint32_t *__restrict__ ranks,
+                  uint32_t *__restrict__ meta, uint32_t policy, uint32_t log2_sites,
+                  uint32_t sites, uint32_t T)
+{
+    __shared__ uint32_t h[256];
+    const uint32_t k = threadIdx.x;
+    if (k < 256u) h[k] = 0u;
+    __syncthreads();
+    for (uint32_t t = k; t < T; t += blockDim.x) {
+        const int site = curation_site(policy, log2_sites, sites, t);
+        if (site >= 0) atomicMax(&h[site], t + 1u);
+    }
+    __syncthreads();
+    const uint32_t mine = k < sites ? h[k] : 0u;
+    const int m = __syncthreads_count(mine != 0u);
+    if (mine != 0u) {
+        uint32_t pos = 0;
+        for (uint32_t q = 0; q < sites; ++q) pos += (h[q] != 0u && h[q] < mine) ? 1u : 0u;
+        order[pos] = k;
+        ranks[pos] = mine - 1u;
+    }
+    if (k == 0) meta[0] = static_cast<uint32_t>(m);
+}
+
+// Retained ranks at counter T, sorted (order, ranks, meta[0] = m); returns the launches made.
+int launch_rank_order(uint32_t *holder, uint32_t *order, uint32_t *ranks, uint32_t *meta,
+                      uint32_t policy, uint32_t log2_sites, uint32_t sites, uint32_t T,
+                      cudaStream_t stream)
+{
+    if (T <= kFusedRankMax) {
+        rank_order_kernel<<<1, 1024, 0, stream>>>(order, ranks, meta, policy, log2_sites, sites, T);
+        return 1;
+    }
+    if (cudaMemsetAsync(holder, 0, sites * sizeof(uint32_t), stream) != cudaSuccess) return 0;
+    uint32_t blocks = (T + 255u) / 256u;
+    if (blocks > 4096u) blocks = 4096u;
+    rank_kernel<<<blocks, 256, 0, stream>>>(holder, policy, log2_sites, sites, T);
+    order_kernel<<<1, 256, 0, stream>>>(holder, order, ranks, meta, sites);
+    return 2;
+}
+
 // One warp per sampled agent: lanes 0..7 hold the agent's surface words; for packed word w,
 // lane l gathers differentia index w * (32/b) + l (site order[i], fetched from the lane that
 // holds its surface word) and one warp OR-reduction assembles the word.
@@ -120,9 +168,14 @@ __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_wo
     if (lane < kPackWords) packed[static_cast<size_t>(a) * kPackWords + lane] = word_out;
 }
 
-// One thread per pair: block (x, y) covers row i = y and columns j = i + 1 + 256 x + t.  The
-// first set bit of packed[i] ^ packed[j] gives the first mismatching rank index i*.  WIDE:
-// the rank-ordered strings need more than 64 bits (otherwise one 64-bit word decides).
+// Pairs in output order, each warp a contiguous stretch of them: lane t takes pairs
+// base + t, base + t + 32, ..., so a warp's (lo, hi) writes are contiguous.  A lane finds
+// the row of its first pair once -- row i holds pairs off(i) <= p < off(i + 1) with
+// off(i) = i (2n - i - 1) / 2; a single-precision root of i^2 - (2n - 1) i + 2p = 0 from the
+// exact 64-bit discriminant is within one row, and integer comparisons correct it -- then
+// steps 32 pairs at a time, carrying into the next rows when j passes n - 1.  The first set
+// bit of packed[i] ^ packed[j] gives the first mismatching rank index i*.  WIDE: the
+// rank-ordered strings need more than 64 bits (otherwise one 64-bit word decides).
 template <bool WIDE>
 __global__ void __launch_bounds__(kPairThreads)
 pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__restrict__ ranks_g,
@@ -130,47 +183,64 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
             uint32_t *__restrict__ lo, uint32_t *__restrict__ hi)
 {
     __shared__ uint32_t ranks[256];
-    __shared__ uint32_t mine[kPackWords];
     const uint32_t m = meta[0];
-    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ranks[i] = ranks_g[i];
-    for (uint32_t row = blockIdx.y; row < n; row += gridDim.y) {
-        const uint32_t j0 = row + 1u + blockIdx.x * kPairThreads;
-        if (j0 >= n) continue;  // uniform across the block
-        if (threadIdx.x < kPackWords) mine[threadIdx.x] = packed[static_cast<size_t>(row) * kPackWords + threadIdx.x];
-        __syncthreads();
-        const uint32_t j = j0 + threadIdx.x;
-        if (j < n) {
-            const uint32_t *pj = packed + static_cast<size_t>(j) * kPackWords;
-            uint32_t first_bit = 0xFFFFFFFFu;
-            if constexpr (!WIDE) {
-                const uint2 b0 = __ldg(reinterpret_cast<const uint2 *>(pj));
-                const unsigned long long x =
-                    (static_cast<unsigned long long>(b0.y ^ mine[1]) << 32) | (b0.x ^ mine[0]);
-                if (x != 0ull) first_bit = static_cast<uint32_t>(__ffsll(static_cast<long long>(x)) - 1);
-            } else {
-                const uint4 b0 = __ldg(reinterpret_cast<const uint4 *>(pj));
-                const uint4 b1 = __ldg(reinterpret_cast<const uint4 *>(pj) + 1);
-                const uint32_t x[kPackWords] = {b0.x ^ mine[0], b0.y ^ mine[1], b0.z ^ mine[2],
-                                                b0.w ^ mine[3], b1.x ^ mine[4], b1.y ^ mine[5],
-                                                b1.z ^ mine[6], b1.w ^ mine[7]};
+    for (uint32_t r = threadIdx.x; r < m; r += blockDim.x) ranks[r] = ranks_g[r];
+    __syncthreads();
+    const unsigned long long n_pairs = static_cast<unsigned long long>(n) * (n - 1u) / 2ull;
+    const unsigned long long n_warps = static_cast<unsigned long long>(gridDim.x) * (kPairThreads / 32);
+    const unsigned long long per_warp = ((n_pairs + n_warps - 1ull) / n_warps + 31ull) / 32ull * 32ull;
+    const unsigned long long warp = (static_cast<unsigned long long>(blockIdx.x) * kPairThreads + threadIdx.x) >> 5;
+    unsigned long long p = warp * per_warp + (threadIdx.x & 31u);
+    const unsigned long long p_end = (warp + 1ull) * per_warp < n_pairs ? (warp + 1ull) * per_warp : n_pairs;
+    if (p >= p_end) return;
+
+    const unsigned long long b = 2ull * n - 1ull;  // off(r) = r (b - r) / 2
+    const float est = (static_cast<float>(b) - sqrtf(static_cast<float>(b * b - 8ull * p))) * 0.5f;
+    uint32_t i = est > 0.0f ? static_cast<uint32_t>(est) : 0u;
+    if (i > n - 2u) i = n - 2u;
+    while (i > 0u && static_cast<unsigned long long>(i) * (b - i) / 2ull > p) --i;
+    while (i + 2u < n && static_cast<unsigned long long>(i + 1u) * (b - i - 1u) / 2ull <= p) ++i;
+    uint32_t j = i + 1u + static_cast<uint32_t>(p - static_cast<unsigned long long>(i) * (b - i) / 2ull);
+
+    for (;;) {
+        const uint32_t *pi = packed + static_cast<size_t>(i) * kPackWords;
+        const uint32_t *pj = packed + static_cast<size_t>(j) * kPackWords;
+        uint32_t first_bit = 0xFFFFFFFFu;
+        if constexpr (!WIDE) {
+            const uint2 a0 = __ldg(reinterpret_cast<const uint2 *>(pi));
+            const uint2 b0 = __ldg(reinterpret_cast<const uint2 *>(pj));
+            const unsigned long long x =
+                (static_cast<unsigned long long>(b0.y ^ a0.y) << 32) | (b0.x ^ a0.x);
+            if (x != 0ull) first_bit = static_cast<uint32_t>(__ffsll(static_cast<long long>(x)) - 1);
+        } else {
+            const uint4 a0 = __ldg(reinterpret_cast<const uint4 *>(pi));
+            const uint4 a1 = __ldg(reinterpret_cast<const uint4 *>(pi) + 1);
+            const uint4 b0 = __ldg(reinterpret_cast<const uint4 *>(pj));
+            const uint4 b1 = __ldg(reinterpret_cast<const uint4 *>(pj) + 1);
+            const uint32_t x[kPackWords] = {b0.x ^ a0.x, b0.y ^ a0.y, b0.z ^ a0.z, b0.w ^ a0.w,
+                                            b1.x ^ a1.x, b1.y ^ a1.y, b1.z ^ a1.z, b1.w ^ a1.w};
 #pragma unroll
-                for (int w = kPackWords - 1; w >= 0; --w)
-                    if (x[w] != 0u) first_bit = 32u * w + (__ffs(x[w]) - 1u);
-            }
-            uint32_t l, h;
-            if (first_bit == 0xFFFFFFFFu) {
-                h = T;
-                l = m >= K ? ranks[m - K] + 1u : 0u;
-            } else {
-                const uint32_t istar = first_bit >> log2_bits;  // first mismatch, 0-based
-                h = ranks[istar];
-                l = istar >= K ? ranks[istar - K] + 1u : 0u;
-            }
-            const size_t p = static_cast<size_t>(row) * (2ull * n - row - 1ull) / 2ull + (j - row - 1u);
-            __stcs(&lo[p], l);
-            __stcs(&hi[p], h);
+            for (int w = kPackWords - 1; w >= 0; --w)
+                if (x[w] != 0u) first_bit = 32u * w + (__ffs(x[w]) - 1u);
         }
-        __syncthreads();  // `mine` is rewritten for the next row
+        uint32_t l, h;
+        if (first_bit == 0xFFFFFFFFu) {
+            h = T;
+            l = m >= K ? ranks[m - K] + 1u : 0u;
+        } else {
+            const uint32_t istar = first_bit >> log2_bits;  // first mismatch, 0-based
+            h = ranks[istar];
+            l = istar >= K ? ranks[istar - K] + 1u : 0u;
+        }
+        __stcs(&lo[p], l);
+        __stcs(&hi[p], h);
+        p += 32u;
+        if (p >= p_end) break;
+        j += 32u;
+        while (j >= n) {  // past the end of row i: pair (i + 1, i + 2) follows (i, n - 1)
+            j = j - n + i + 2u;
+            ++i;
+        }
     }
 }
 
@@ -183,7 +253,10 @@ void launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, uint32_t 
 {
     pack_kernel<<<(n + 7u) / 8u, 256, 0, stream>>>(pop, record_words, n_agents, d_ids, n, order,
                                                    meta, bits, T, packed, status);
-    const dim3 grid((n + kPairThreads - 1) / kPairThreads, n < 65535u ? n : 65535u);
+    // enough resident blocks for the whole GPU, each thread then sweeping several pairs
+    const unsigned long long pairs = static_cast<unsigned long long>(n) * (n - 1u) / 2ull;
+    const unsigned long long want = (pairs + kPairThreads - 1) / kPairThreads;
+    const uint32_t grid = static_cast<uint32_t>(want < kPairGrid ? want : kPairGrid);
     const uint32_t log2_bits = bits == 1u ? 0u : bits == 2u ? 1u : bits == 4u ? 2u : 3u;
     // sites * bits <= 64: every rank-ordered string fits in its first 64 bits
     if (sites * bits <= 64u)
@@ -410,17 +483,10 @@ cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t
     const uint32_t S = run->cfg.surface_sites, b = run->cfg.differentia_bits;
     const uint32_t T = static_cast<uint32_t>(run->generation);
     MrcaLayout l = carve(scratch, S, n);
-    cudaError_t e = cudaMemsetAsync(l.holder, 0, S * sizeof(uint32_t), run->stream);
-    if (e != cudaSuccess) return e;
-    if (T > 0) {
-        uint32_t blocks = (T + 255u) / 256u;
-        if (blocks > 4096u) blocks = 4096u;
-        rank_kernel<<<blocks, 256, 0, run->stream>>>(l.holder, run->cfg.curation,
-                                                     run->log2_sites, S, T);
-        run->launches += 1;
-    }
-    order_kernel<<<1, 256, 0, run->stream>>>(l.holder, l.order, l.ranks, l.meta, S);
-    run->launches += 1;
+    const int made = launch_rank_order(l.holder, l.order, l.ranks, l.meta, run->cfg.curation,
+                                       run->log2_sites, S, T, run->stream);
+    if (made == 0) return cudaErrorUnknown;
+    run->launches += made;
     launch_pack_and_pairs(reinterpret_cast<const uint32_t *>(run->pop[run->cur]),
                           run->record_bytes / 4u, run->n_agents, d_ids, n, l.order, l.ranks,
                           l.meta, S, b, margin(b), T, l.packed, d_lo, d_hi, run->d_status,
@@ -509,14 +575,9 @@ extern "C" int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_byt
     while ((1u << log2_sites) < S) ++log2_sites;
 
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess ||
-        cudaMemsetAsync(l.holder, 0, S * sizeof(uint32_t), st) != cudaSuccess)
+        launch_rank_order(l.holder, l.order, l.ranks, l.meta, curation, log2_sites, S,
+                          generation, st) == 0)
         return GA_ECUDA;
-    if (generation > 0u) {
-        uint32_t blocks = (generation + 255u) / 256u;
-        if (blocks > 4096u) blocks = 4096u;
-        rank_kernel<<<blocks, 256, 0, st>>>(l.holder, curation, log2_sites, S, generation);
-    }
-    order_kernel<<<1, 256, 0, st>>>(l.holder, l.order, l.ranks, l.meta, S);
     launch_pack_and_pairs(static_cast<const uint32_t *>(d_records), record_bytes / 4u, n_agents,
                           d_agent_ids, n, l.order, l.ranks, l.meta, S, b, margin(b), generation,
                           l.packed, d_lo, d_hi, status, st);

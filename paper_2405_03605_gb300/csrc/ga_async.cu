@@ -118,6 +118,8 @@ __device__ __forceinline__ void refill128(uint4 *p, const uint32_t (&v)[4])
                  : "=l"(lo), "=l"(hi)
                  : "l"(ones), "l"(ones), "l"(pack64(v[0], v[1])), "l"(pack64(v[2], v[3])), "l"(p)
                  : "memory");
+    (void)lo;
+    (void)hi;
 }
 
 constexpr int kAsyncThreads = 256;

@@ -173,9 +173,11 @@ __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_wo
 // the row of its first pair once -- row i holds pairs off(i) <= p < off(i + 1) with
 // off(i) = i (2n - i - 1) / 2; a single-precision root of i^2 - (2n - 1) i + 2p = 0 from the
 // exact 64-bit discriminant is within one row, and integer comparisons correct it -- then
-// steps 32 pairs at a time, carrying into the next rows when j passes n - 1.  The first set
-// bit of packed[i] ^ packed[j] gives the first mismatching rank index i*.  WIDE: the
-// rank-ordered strings need more than 64 bits (otherwise one 64-bit word decides).
+// steps 32 pairs at a time, carrying into the next rows when j passes n - 1, and reloads row
+// i's string only when i changes.  Pair indices fit 32 bits (n <= 65536: fewer than 2^31
+// pairs).  The first set bit of packed[i] ^ packed[j] gives the first mismatching rank index
+// i*.  WIDE: the rank-ordered strings need more than 64 bits (otherwise one 64-bit word
+// decides).
 template <bool WIDE>
 __global__ void __launch_bounds__(kPairThreads)
 pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__restrict__ ranks_g,
@@ -201,20 +203,31 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
     while (i > 0u && static_cast<unsigned long long>(i) * (b - i) / 2ull > p) --i;
     while (i + 2u < n && static_cast<unsigned long long>(i + 1u) * (b - i - 1u) / 2ull <= p) ++i;
     uint32_t j = i + 1u + static_cast<uint32_t>(p - static_cast<unsigned long long>(i) * (b - i) / 2ull);
+    uint32_t q = static_cast<uint32_t>(p);
+    const uint32_t q_end = static_cast<uint32_t>(p_end);
 
+    uint32_t row = 0xFFFFFFFFu;  // row whose string a0 (, a1) holds
+    uint2 a0n = make_uint2(0u, 0u);
+    uint4 a0 = make_uint4(0u, 0u, 0u, 0u), a1 = a0;
     for (;;) {
-        const uint32_t *pi = packed + static_cast<size_t>(i) * kPackWords;
         const uint32_t *pj = packed + static_cast<size_t>(j) * kPackWords;
+        if (i != row) {
+            const uint32_t *pi = packed + static_cast<size_t>(i) * kPackWords;
+            if constexpr (!WIDE) {
+                a0n = __ldg(reinterpret_cast<const uint2 *>(pi));
+            } else {
+                a0 = __ldg(reinterpret_cast<const uint4 *>(pi));
+                a1 = __ldg(reinterpret_cast<const uint4 *>(pi) + 1);
+            }
+            row = i;
+        }
         uint32_t first_bit = 0xFFFFFFFFu;
         if constexpr (!WIDE) {
-            const uint2 a0 = __ldg(reinterpret_cast<const uint2 *>(pi));
             const uint2 b0 = __ldg(reinterpret_cast<const uint2 *>(pj));
             const unsigned long long x =
-                (static_cast<unsigned long long>(b0.y ^ a0.y) << 32) | (b0.x ^ a0.x);
+                (static_cast<unsigned long long>(b0.y ^ a0n.y) << 32) | (b0.x ^ a0n.x);
             if (x != 0ull) first_bit = static_cast<uint32_t>(__ffsll(static_cast<long long>(x)) - 1);
         } else {
-            const uint4 a0 = __ldg(reinterpret_cast<const uint4 *>(pi));
-            const uint4 a1 = __ldg(reinterpret_cast<const uint4 *>(pi) + 1);
             const uint4 b0 = __ldg(reinterpret_cast<const uint4 *>(pj));
             const uint4 b1 = __ldg(reinterpret_cast<const uint4 *>(pj) + 1);
             const uint32_t x[kPackWords] = {b0.x ^ a0.x, b0.y ^ a0.y, b0.z ^ a0.z, b0.w ^ a0.w,
@@ -232,10 +245,10 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
             h = ranks[istar];
             l = istar >= K ? ranks[istar - K] + 1u : 0u;
         }
-        __stcs(&lo[p], l);
-        __stcs(&hi[p], h);
-        p += 32u;
-        if (p >= p_end) break;
+        __stcs(&lo[q], l);
+        __stcs(&hi[q], h);
+        q += 32u;
+        if (q >= q_end) break;
         j += 32u;
         while (j >= n) {  // past the end of row i: pair (i + 1, i + 2) follows (i, n - 1)
             j = j - n + i + 2u;

@@ -368,7 +368,7 @@ def run_ours(args, rank, world, local):
         "mrca": {"ms_per_run": mrca_ms, "pairs": pairs, "bytes_written": 8 * pairs,
                  "achieved": 8 * pairs / (mrca_ms / 1000.0) / 1e9, "peak": peak, "unit": "GB/s",
                  "frac": 8 * pairs / (mrca_ms / 1000.0) / 1e9 / peak,
-                 "note": "all four MRCA kernels per call; bound by the (lo, hi) output writes"},
+                 "note": "every MRCA kernel of the call (replay and rank sort, pack, pairs); bound by the (lo, hi) output writes"},
         "treatment_contrast": contrast,
         "batched_vs_serial": batched,
         **({"serving": served} if served is not None else {}),

@@ -511,7 +511,7 @@ cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t
 }  // namespace ga
 
 // ---------------------------------------------------------------------------------------
-// ga_mrca_bounds_noalloc: the same four MRCA kernels with their scratch held in a fixed
+// ga_mrca_bounds_noalloc: the same MRCA kernels with their scratch held in a fixed
 // device array instead of memory allocated per call, for callers that cannot allocate
 // device memory (see include/ga.h).
 //

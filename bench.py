@@ -148,8 +148,10 @@ class Clocks:
 
 
 # DRAM bytes (read + write) of one island_step_kernel<32,2,5> launch on the 512x1024x32 grid:
-# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this kernel build.
+# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this kernel build, and
+# its warp-instructions per island-generation (smsp__inst_executed.sum / 524,288 islands).
 ISLAND_STEP_TRAFFIC = {"kernel": "island_step_kernel<32,2,5>", "bytes": 494.2e6,
+                       "inst_per_island_gen": 111.0e6 / 524288,
                        "rows": 512, "cols": 1024, "island_size": 32}
 
 
@@ -333,6 +335,17 @@ def run_ours(args, rank, world, local):
             contrast["adaptive" if sh.p_ben > 0 else "purifying"] = depth
     contrast["unit"] = "generations (mean over sampled pairs of T - hi)"
 
+    # issue roofline of the same kernel: warp-instructions issued per second against the SM
+    # issue limit (one warp-instruction per clock on each of the 4 sub-partitions of each SM)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    issue = None
+    if same_shape:
+        inst_rate = ISLAND_STEP_TRAFFIC["inst_per_island_gen"] * shs[0].n_islands / avg_launch_s
+        issue = {"bound": "alu", "unit": "warp-instr/s", "achieved": inst_rate,
+                 "per_unit": ISLAND_STEP_TRAFFIC["inst_per_island_gen"],
+                 "unit_of_work": "island-generation (ncu smsp__inst_executed.sum of this build)",
+                 "sms": n_sm}
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(args, shs, ids_h, world)
@@ -349,6 +362,11 @@ def run_ours(args, rank, world, local):
 
     if rank != 0:
         return
+    if issue is not None:
+        mhz = (clk or {}).get("sm_mhz") or 2070.0  # sampled median SM clock, else the maximum
+        issue["peak"] = issue["sms"] * 4 * mhz * 1e6
+        issue["frac"] = issue["achieved"] / issue["peak"]
+        issue["clock_mhz"] = mhz
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(args, shs[0], args.cpu_seconds)
@@ -365,6 +383,7 @@ def run_ours(args, rank, world, local):
                      "peak_kind": f"{peak_kind} copy bandwidth",
                      "bytes_per_launch": bytes_per_launch,
                      "avg_launch_us": avg_launch_s * 1e6},
+        "issue_roofline": issue,
         "mrca": {"ms_per_run": mrca_ms, "pairs": pairs, "bytes_written": 8 * pairs,
                  "achieved": 8 * pairs / (mrca_ms / 1000.0) / 1e9, "peak": peak, "unit": "GB/s",
                  "frac": 8 * pairs / (mrca_ms / 1000.0) / 1e9 / peak,

@@ -1,6 +1,7 @@
 """GPU (CUDA library, through the C ABI) versus the CPU oracle, bit-exact on every trait,
 counter and surface word of every agent.  Sizes span several warps/blocks with ragged tails;
-one case runs the full 512x1024-island grid in the bench's launch configuration."""
+one case runs the full 512x1024-island grid for 100 generations in the bench's launch
+configuration."""
 import hashlib
 import json
 import os
@@ -173,14 +174,15 @@ def test_curation_sites_match_oracle():
 
 
 def test_full_grid_first_generations():
-    """The 512x1024 x 32-agent grid (16,777,216 agents) for 3 generations, compared with the
-    oracle on every agent, in the launch configuration the benchmark times."""
+    """The 512x1024 x 32-agent grid (16,777,216 agents) for 100 generations, compared with the
+    oracle on every agent, in the launch configuration the benchmark times (one launch per
+    generation, migration every generation); then the MRCA bounds of 4,096 sampled agents."""
     shape = PAPER_ADAPTIVE
     g = gpu_run(shape)
-    g.step(3)
+    g.step(100)
     g.sync()
     o = oracle_for(shape)
-    o.step(3)
+    o.step(100)
     got, exp = g.snapshot(), o.snapshot()
     assert_same(got, exp, 32)
     ids = sample_agent_ids(shape.n_agents, 4096, seed=42)

@@ -299,14 +299,14 @@ __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &
             const uint32_t mine = seg_lane + 32u * ag;
             const int from = sl.x == mine ? 0 : sl.y == mine ? 1 : sl.z == mine ? 2
                            : sl.w == mine ? 3 : -1;
-            if (from >= 0) {
+            {  // branch-free: every lane reads a slot, the four receivers keep it
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    const uint4 xq = s_imm[4 * local + from][q];
+                    const uint4 xq = s_imm[4 * local + (from < 0 ? 0 : from)][q];
                     const uint32_t w4[4] = {xq.x, xq.y, xq.z, xq.w};
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        if (4 * q + k < LW) rec[ag][4 * q + k] = w4[k];
+                        if (4 * q + k < LW) rec[ag][4 * q + k] = from >= 0 ? w4[k] : rec[ag][4 * q + k];
                 }
             }
         }

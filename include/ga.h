@@ -105,7 +105,8 @@ int ga_config_check(const ga_config *cfg);
 int ga_record_bytes(const ga_config *cfg, uint32_t *bytes);
 
 /* Bytes of device workspace a run of cfg needs (two population buffers plus a header; in the
-   asynchronous modes also four send buffers of 16 + record_bytes bytes per island). */
+   asynchronous modes also four send buffers per island: 16 bytes each for 16-byte records,
+   16 + record_bytes otherwise). */
 int ga_workspace_bytes(const ga_config *cfg, size_t *bytes);
 
 /*
@@ -151,9 +152,10 @@ int ga_migrate_policy(ga_run *run, uint32_t per_neighbor, uint32_t every_k);
  * later blocks is then born in each of them and its counter runs ahead of the generation
  * -- under beneficial mutation such lineages are fitter and take over.  GA_ASYNC_SEQUENTIAL
  * runs each window island by island in index order: a reproducible schedule the CPU model
- * follows exactly.  window in [1, GA_ASYNC_MAX_WINDOW]; the default after ga_create is 1.  Send buffers are emptied by ga_create, ga_reset and
- * ga_load.  Errors: GA_EINVAL (window out of range), GA_ESTATE (run not in an asynchronous
- * mode).
+ * follows exactly.  window in [1, GA_ASYNC_MAX_WINDOW]; the default after ga_create is 1.
+ * Send buffers are emptied by ga_create, ga_reset and ga_load.  Asynchronous kernels exist
+ * for island sizes 16, 32 and 64 (other sizes: GA_EUNSUPPORTED from ga_create).
+ * Errors: GA_EINVAL (window out of range), GA_ESTATE (run not in an asynchronous mode).
  */
 int ga_async_window(ga_run *run, uint32_t window);
 

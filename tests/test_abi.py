@@ -51,6 +51,38 @@ def test_config_checks(lib):
     assert ga.config_check(SMALL_TORUS.with_(island_size=256)) == -6
 
 
+def test_async_config_checks(lib):
+    """Asynchronous modes: kernels for islands of 16, 32 and 64 agents, every record size
+    and both genome models; unknown modes are invalid."""
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import SMALL_TORUS, ASYNC, ASYNC_SEQUENTIAL, \
+        MODEL_FITNESS
+    for mode in (ASYNC, ASYNC_SEQUENTIAL):
+        for n in (16, 32, 64):
+            for sites, bits in ((64, 1), (128, 1), (256, 1), (32, 8)):
+                shape = SMALL_TORUS.with_(mode=mode, island_size=n, surface_sites=sites,
+                                          differentia_bits=bits)
+                assert ga.config_check(shape) == 0, (mode, n, sites, bits)
+            assert ga.config_check(SMALL_TORUS.with_(mode=mode, island_size=n,
+                                                     model=MODEL_FITNESS, p_del=0.33)) == 0
+        for n in (4, 8, 128):
+            assert ga.config_check(SMALL_TORUS.with_(mode=mode, island_size=n)) == -6
+    assert ga.config_check(SMALL_TORUS.with_(mode=3)) == -1
+
+
+def test_async_workspace_sizes(lib):
+    """16-byte records travel through 16-byte buffers, larger ones through a 16-byte flag
+    word plus the record: four per island, after the two population buffers."""
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import SMALL_TORUS, ASYNC
+    for sites, rb in ((64, 16), (128, 32), (256, 48)):
+        sync = SMALL_TORUS.with_(surface_sites=sites)
+        extra = ga.workspace_bytes(sync.with_(mode=ASYNC)) - ga.workspace_bytes(sync)
+        per_buffer = 16 if rb == 16 else 16 + rb
+        want = sync.n_islands * 4 * per_buffer
+        assert want <= extra < want + 256, (sites, extra, want)
+
+
 def test_sizes(lib):
     from paper_2405_03605_gb300 import ga
     from paper_2405_03605_gb300.workloads import SMALL_TORUS, variant_shapes, PAPER_ADAPTIVE

@@ -131,8 +131,33 @@ struct AsyncArgs {
     uint4 *mail;           // [island][4] send buffers (16-byte records: the record itself;
                            // otherwise 1 + Q uint4: flag word, record)
     uint32_t every_k;      // migration on generations g with g mod every_k == 0
+    uint32_t phase0;       // g0 mod every_k
     uint32_t first, last;  // islands [first, last) run in this launch
+    uint32_t cols_m, cols_l;  // island / cols = multiply-shift (cols_l = 0: cols == 1)
 };
+
+// Unsigned division by the torus width as a multiply and shifts, with the magic number of
+// Granlund and Montgomery ("Division by invariant integers using multiplication", PLDI
+// 1994, the round-up method for a 32-bit divisor d >= 2): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> 1)) >> (l - 1) with t = umulhi(m, n).
+void division_magic(uint32_t d, uint32_t &m, uint32_t &l)
+{
+    if (d <= 1u) {
+        m = 0;
+        l = 0;
+        return;
+    }
+    l = 0;
+    while ((1ull << l) < d) ++l;
+    m = static_cast<uint32_t>((((1ull << 32) * ((1ull << l) - d)) / d) + 1ull);
+}
+
+__device__ __forceinline__ uint32_t div_cols(uint32_t n, uint32_t m, uint32_t l)
+{
+    if (l == 0u) return n;  // cols == 1
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> 1)) >> (l - 1u);
+}
 
 // Send-buffer size in uint4 for a record of Q uint4.
 __host__ __device__ constexpr int box_words(int Q) { return Q == 1 ? 1 : 1 + Q; }
@@ -186,7 +211,7 @@ island_async_kernel(const AsyncArgs a)
     const bool sender = seg_lane >= 4u && seg_lane < 8u;
     uint4 *box = nullptr;
     if (taker) {
-        const uint32_t y = island / p.cols, x = island - y * p.cols;
+        const uint32_t y = div_cols(island, a.cols_m, a.cols_l), x = island - y * p.cols;
         const uint32_t yn = d == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
                           : d == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
         const uint32_t xn = d == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
@@ -211,7 +236,7 @@ island_async_kernel(const AsyncArgs a)
         }
     };
     // generations since the last migration generation (g mod every_k), kept incrementally
-    uint32_t phase = p.g0 % a.every_k;
+    uint32_t phase = a.phase0;
     if (early && p.migrate && phase == 0u) prepare();
 
     for (uint32_t it = 0; it < p.n_gens; ++it) {
@@ -435,8 +460,10 @@ cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_
                           static_cast<uint32_t>(run->cfg.seed >> 32)});
     a.mail = reinterpret_cast<uint4 *>(run->mail);
     a.every_k = run->every_k;
+    a.phase0 = g0 % run->every_k;
     a.first = first;
     a.last = last;
+    division_magic(run->cfg.cols, a.cols_m, a.cols_l);
     const uint32_t N = run->cfg.island_size;
     const uint32_t per_block = kAsyncWarps * (N >= 32 ? 1u : 32u / N);
     const uint32_t blocks = (last - first + per_block - 1) / per_block;

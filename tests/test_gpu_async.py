@@ -237,3 +237,28 @@ def test_batch_steps_async_member_alone():
     assert_same(r1.snapshot(), o1.snapshot(), 16)
     assert_same(r2.snapshot(), o2.snapshot(), 32)
     b.close()
+
+
+@pytest.mark.parametrize("sites", [64, 256])  # 16-byte (atomic) and 48-byte (flag) buffers
+def test_reset_and_load_empty_the_buffers(sites):
+    """ga_reset and ga_load empty every send buffer: on the sequential schedule a reset run
+    repeats a fresh run exactly, and a population loaded mid-run continues exactly as the
+    oracle continues from the same records with empty buffers."""
+    shape = RunShape(rows=3, cols=4, island_size=16, surface_sites=sites, seed=41,
+                     mode=ASYNC_SEQUENTIAL, async_window=4)
+    g = gpu_run(shape)
+    g.step(30)
+    g.sync()
+    first = g.snapshot()
+    g.reset()
+    g.step(30)
+    g.sync()
+    assert_same(g.snapshot(), first, 16)
+    # buffers are full after 30 generations; a load must drop them
+    g.load(first, 30)
+    g.step(20)
+    g.sync()
+    o = oracle_for(shape)
+    o.load(first, 30)
+    o.step_async(20, window=4)
+    assert_same(g.snapshot(), o.snapshot(), 16)

@@ -387,6 +387,144 @@ island_async_kernel(const AsyncArgs a)
     }
 }
 
+// One generation of 16-byte-record islands (a window of 1), migration bookkeeping shared by
+// the block as in the synchronous kernel: thread t < 4 * islands-per-block serves island
+// t / 4 and direction d = t % 4 -- it recomputes that island's slot-d birth draw (bits
+// 16..31: the landing draw), takes the genome out of the neighbour's buffer facing the island
+// with one 128-bit exchange, and resolves the landing slot with its three sibling lanes; the
+// genomes and slots reach the island warps through shared memory.  The island warps then
+// land the arrivals, refill their own buffers (lanes 4..7, compare-and-swap) from the island
+// as it now stands, and reproduce.  Every take of the launch precedes every refill (block
+// barrier), so an island that is its own neighbour takes what it sent in the previous
+// generation, as in the one-warp kernel.
+template <int N, int TS, int MODEL>
+__global__ void __launch_bounds__(kAsyncThreads) island_async_gen_kernel(const AsyncArgs a)
+{
+    constexpr int A = Shape<N>::A, P = Shape<N>::P, SEG = Shape<N>::SEG;
+    constexpr int LW = 4;                    // 16-byte records
+    constexpr int BI = kAsyncWarps * P;      // islands per block
+    constexpr int ML = BI * 4;               // bookkeeping lanes: (island, direction)
+    constexpr uint32_t kNone = 0xFFFFFFFFu;  // no arrival from that direction
+    __shared__ uint4 s_got[ML];
+    __shared__ __align__(16) uint32_t s_slot[ML];
+    const RunParams &p = a.r;
+    const uint32_t g = p.g0;
+
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t seg_lane = lane % SEG;
+    const uint32_t local = (threadIdx.x >> 5) * P + lane / SEG;
+    const uint32_t island0 = a.first + blockIdx.x * BI;
+    const uint32_t island = island0 + local;
+    const bool valid = island < a.last;
+    const unsigned mask = __ballot_sync(0xffffffffu, valid);
+    const bool mig = p.migrate && a.phase0 == 0u;
+
+    // Bookkeeping, part 1: the takes are issued first, so their latency overlaps the island
+    // warps' record loads and birth draws.
+    const bool bk = mig && threadIdx.x < ML;
+    const unsigned bk_mask = __ballot_sync(0xffffffffu, bk);
+    const uint32_t md = threadIdx.x & 3u;
+    uint32_t r = md;
+    uint4 got = make_uint4(~0u, ~0u, ~0u, ~0u);
+    if (bk) {
+        const uint32_t isl = island0 + (threadIdx.x >> 2);
+        if (isl < a.last) {
+            const uint32_t u = philox_rk(g, isl, md | (kBirth << 16), p.run_id, a.rk).w;
+            r = md + (((u >> 16) * static_cast<uint32_t>(N - md)) >> 16);
+            const uint32_t y = div_cols(isl, a.cols_m, a.cols_l), x = isl - y * p.cols;
+            const uint32_t yn = md == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
+                              : md == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
+            const uint32_t xn = md == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
+                              : md == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
+            got = take128(a.mail + (static_cast<size_t>(yn * p.cols + xn) * 4u + (md ^ 1u)));
+        }
+    }
+
+    uint32_t rec[A][LW];
+    uint4 w[A];
+    if (valid) {
+#pragma unroll
+        for (int ag = 0; ag < A; ++ag) {
+            const uint4 v = __ldg(&p.src[static_cast<size_t>(island) * N + seg_lane + 32u * ag]);
+            rec[ag][0] = v.x;
+            rec[ag][1] = v.y;
+            rec[ag][2] = v.z;
+            rec[ag][3] = v.w;
+        }
+        birth_draws<N>(w, p, a.rk, g, island, seg_lane);
+    }
+
+    // Bookkeeping, part 2: the partial Fisher-Yates landing slots among the island's four
+    // lanes (entry e: "position r[e] now holds value v[e]", later entries winning); a
+    // direction with nothing to deliver keeps its swap but lands nothing.
+    if (mig) {
+        if (bk) {
+            uint32_t rr[4];
+#pragma unroll
+            for (int dd = 0; dd < 4; ++dd) rr[dd] = __shfl_sync(bk_mask, r, dd, 4);
+            uint32_t v[4], slot = 0;
+#pragma unroll
+            for (int dd = 0; dd < 4; ++dd) {
+                uint32_t vd = dd, vr = rr[dd];
+#pragma unroll
+                for (int e = 0; e < dd; ++e) {
+                    if (rr[e] == static_cast<uint32_t>(dd)) vd = v[e];
+                    if (rr[e] == rr[dd]) vr = v[e];
+                }
+                if (static_cast<uint32_t>(dd) == md) slot = vr;
+                v[dd] = vd;
+            }
+            s_got[threadIdx.x] = got;
+            s_slot[threadIdx.x] = got.y != kNeverSent ? slot : kNone;
+        }
+        __syncthreads();
+    }
+    if (!valid) return;
+
+    if (mig) {
+        // land (branch-free: every lane reads a slot, the receivers keep it)
+        const uint4 sl = *reinterpret_cast<const uint4 *>(&s_slot[4 * local]);
+#pragma unroll
+        for (int ag = 0; ag < A; ++ag) {
+            const uint32_t mine = seg_lane + 32u * ag;
+            const int from = sl.x == mine ? 0 : sl.y == mine ? 1 : sl.z == mine ? 2
+                           : sl.w == mine ? 3 : -1;
+            const uint4 xq = s_got[4 * local + (from < 0 ? 0 : from)];
+            rec[ag][0] = from >= 0 ? xq.x : rec[ag][0];
+            rec[ag][1] = from >= 0 ? xq.y : rec[ag][1];
+            rec[ag][2] = from >= 0 ? xq.z : rec[ag][2];
+            rec[ag][3] = from >= 0 ? xq.w : rec[ag][3];
+        }
+        // refill: lane 4 + d copies member e_d of the island as it now stands into its
+        // buffer towards d if that is empty
+        const uint32_t d = seg_lane & 3u;
+        const uint32_t u = __shfl_sync(mask, w[0].w, static_cast<int>(d), SEG);
+        const uint32_t e = (((u >> 8) & 0xFFu) * N) >> 8;
+        uint32_t out[LW];
+#pragma unroll
+        for (int k = 0; k < LW; ++k) {
+            if constexpr (N <= 32) {
+                out[k] = __shfl_sync(mask, rec[0][k], static_cast<int>(e), SEG);
+            } else {
+                uint32_t val = 0;
+#pragma unroll
+                for (int q = 0; q < A; ++q) {
+                    const uint32_t xv = __shfl_sync(mask, rec[q][k], static_cast<int>(e & 31u));
+                    if ((e >> 5) == static_cast<uint32_t>(q)) val = xv;
+                }
+                out[k] = val;
+            }
+        }
+        if (seg_lane >= 4u && seg_lane < 8u && out[1] != kNeverSent)
+            refill128(a.mail + (static_cast<size_t>(island) * 4u + d), out);
+    }
+    reproduce<N, 2, TS, MODEL>(rec, w, p, a.rk, island, seg_lane, mask, g, __ldg(&p.gen_sites[0]));
+#pragma unroll
+    for (int ag = 0; ag < A; ++ag)
+        p.dst[static_cast<size_t>(island) * N + seg_lane + 32u * ag] =
+            make_uint4(rec[ag][0], rec[ag][1], rec[ag][2], rec[ag][3]);
+}
+
 using AsyncKernel = void (*)(AsyncArgs);
 
 template <int N, int TS>
@@ -413,6 +551,25 @@ AsyncKernel pick_async(uint32_t island_size, uint32_t surface_words, uint32_t ts
     case 16: return pick_async_ts<16>(surface_words, tsize, model);
     case 32: return pick_async_ts<32>(surface_words, tsize, model);
     case 64: return pick_async_ts<64>(surface_words, tsize, model);
+    default: return nullptr;
+    }
+}
+
+// One-generation launches of 16-byte records.
+template <int N>
+AsyncKernel pick_async_gen_n(uint32_t tsize, uint32_t model)
+{
+    if (model == GA_MODEL_FITNESS)
+        return tsize == 5u ? island_async_gen_kernel<N, 5, 1> : island_async_gen_kernel<N, 0, 1>;
+    return tsize == 5u ? island_async_gen_kernel<N, 5, 0> : island_async_gen_kernel<N, 0, 0>;
+}
+
+AsyncKernel pick_async_gen(uint32_t island_size, uint32_t tsize, uint32_t model)
+{
+    switch (island_size) {
+    case 16: return pick_async_gen_n<16>(tsize, model);
+    case 32: return pick_async_gen_n<32>(tsize, model);
+    case 64: return pick_async_gen_n<64>(tsize, model);
     default: return nullptr;
     }
 }
@@ -451,8 +608,12 @@ cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_
                                 uint32_t n_gens, uint32_t first, uint32_t last,
                                 cudaStream_t stream)
 {
-    const AsyncKernel k = pick_async(run->cfg.island_size, run->surface_words,
-                                     run->cfg.tournament_size, run->cfg.model);
+    // a single generation of 16-byte records: the block-cooperative kernel
+    const AsyncKernel k =
+        n_gens == 1u && atomic_buffers(run->record_bytes)
+            ? pick_async_gen(run->cfg.island_size, run->cfg.tournament_size, run->cfg.model)
+            : pick_async(run->cfg.island_size, run->surface_words, run->cfg.tournament_size,
+                         run->cfg.model);
     if (!k || first >= last || last > run->n_islands) return cudaErrorInvalidValue;
     AsyncArgs a;
     a.r = run_params(run, src, dst, g0, n_gens, run->per_neighbor != 0);

@@ -35,7 +35,8 @@ def _sequential_both(shape, calls):
 # drift: the oracle's end state holds agents of different counters (genomes that arrived
 # late survived), so those cases exercise deposits at counters other than the generation.
 # 16-byte records take the atomic handoff, 32/48-byte ones the flag handoff; tori with one
-# row or column (an island its own neighbour) take the in-generation ordering.
+# row or column (an island its own neighbour) take the in-generation ordering; one-generation
+# launches of 16-byte records take the block-cooperative kernel.
 @pytest.mark.parametrize("rows,cols,N,S,b,policy,window,every,drift", [
     (1, 1, 16, 64, 1, STEADY, 5, 1, True),
     (1, 2, 32, 64, 1, STEADY, 3, 1, True),
@@ -45,6 +46,11 @@ def _sequential_both(shape, calls):
     (4, 3, 16, 32, 8, TILTED, 1, 1, True),
     (3, 1, 32, 128, 1, HYBRID, 8, 3, True),
     (2, 5, 64, 16, 2, STEADY, 11, 2, False),
+    # window 1, 16-byte records: the block-cooperative one-generation kernel
+    (3, 5, 16, 64, 1, STEADY, 1, 1, True),
+    (1, 2, 32, 64, 1, STEADY, 1, 1, True),
+    (2, 3, 64, 64, 1, TILTED, 1, 2, True),
+    (4, 4, 32, 32, 2, HYBRID, 1, 1, True),
 ])
 def test_sequential_matches_oracle(rows, cols, N, S, b, policy, window, every, drift):
     shape = RunShape(rows=rows, cols=cols, island_size=N, surface_sites=S, differentia_bits=b,

@@ -64,12 +64,24 @@ def test_sequential_matches_oracle(rows, cols, N, S, b, policy, window, every, d
     assert (len(np.unique(c)) > 1) == drift
 
 
-def test_sequential_fitness_model_matches_oracle():
+@pytest.mark.parametrize("window", [6, 1])
+def test_sequential_fitness_model_matches_oracle(window):
     shape = RunShape(rows=3, cols=4, island_size=32, p_ben=0.003, p_del=0.33,
                      model=MODEL_FITNESS, seed=17, run_id=5, mode=ASYNC_SEQUENTIAL,
-                     async_window=6)
+                     async_window=window)
     got, exp, _ = _sequential_both(shape, [50])
     assert_same(got, exp, 32)
+
+
+@pytest.mark.parametrize("tsize,N", [(3, 16), (8, 32), (1, 64)])
+@pytest.mark.parametrize("window", [1, 4])
+def test_sequential_tournament_sizes(tsize, N, window):
+    """Tournament sizes other than the compiled-in 5, in both kernels (window 1: the
+    one-generation kernel; window 4: the multi-generation kernel)."""
+    shape = RunShape(rows=3, cols=3, island_size=N, tournament_size=tsize, seed=23 + tsize,
+                     p_ben=0.05, p_del=0.05, mode=ASYNC_SEQUENTIAL, async_window=window)
+    got, exp, _ = _sequential_both(shape, [21])
+    assert_same(got, exp, N)
 
 
 @pytest.mark.parametrize("N", [16, 32, 64])

@@ -108,7 +108,7 @@ __device__ __forceinline__ uint4 take128(uint4 *p)
 // outcome is not needed, so the caller never waits for it.
 __device__ __forceinline__ void refill128(uint4 *p, const uint32_t (&v)[4])
 {
-    unsigned long long lo, hi;
+    [[maybe_unused]] unsigned long long lo, hi;
     const unsigned long long ones = ~0ull;
     asm volatile("{\n\t.reg .b128 cv, nv, ov;\n\t"
                  "mov.b128 cv, {%2, %3};\n\t"
@@ -118,8 +118,6 @@ __device__ __forceinline__ void refill128(uint4 *p, const uint32_t (&v)[4])
                  : "=l"(lo), "=l"(hi)
                  : "l"(ones), "l"(ones), "l"(pack64(v[0], v[1])), "l"(pack64(v[2], v[3])), "l"(p)
                  : "memory");
-    (void)lo;
-    (void)hi;
 }
 
 constexpr int kAsyncThreads = 256;

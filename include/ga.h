@@ -50,6 +50,8 @@ extern "C" {
                                 sampled agents differ, so no common rank table exists)   */
 #define GA_EUNSUPPORTED (-6) /* valid configuration with no compiled kernel for it       */
 #define GA_ERANGE (-7)       /* caller buffer too small                                  */
+#define GA_EBOUNDS (-8)      /* a device index check failed; only builds with device checks
+                                (libga_debug.so) test indices, skipping the access      */
 
 /* Curation policy: which surface site the deposit of generation T overwrites. */
 #define GA_STEADY 0u /* evenly spaced retained ranks (gap <= 2T/S), any T                */

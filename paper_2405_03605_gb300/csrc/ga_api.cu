@@ -423,6 +423,7 @@ const char *ga_strerror(int code)
     case GA_ESTATE: return "device state does not allow the request";
     case GA_EUNSUPPORTED: return "configuration has no compiled kernel";
     case GA_ERANGE: return "caller buffer too small";
+    case GA_EBOUNDS: return "device index check failed";
     default: return "unknown error";
     }
 }

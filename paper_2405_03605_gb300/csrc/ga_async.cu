@@ -214,7 +214,9 @@ island_async_kernel(const AsyncArgs a)
                           : d == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
         const uint32_t xn = d == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
                           : d == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
-        box = a.mail + (static_cast<size_t>(yn * p.cols + xn) * 4u + (d ^ 1u)) * MB;
+        const uint32_t nb = yn * p.cols + xn;
+        box = a.mail + (static_cast<size_t>(in_bounds(nb < p.n_islands, p.status) ? nb : island) * 4u +
+                        (d ^ 1u)) * MB;
     } else if (sender) {
         box = a.mail + (static_cast<size_t>(island) * 4u + d) * MB;
     }
@@ -366,7 +368,7 @@ island_async_kernel(const AsyncArgs a)
         if (early && p.migrate && it + 1u < p.n_gens && phase == 0u) prepare();
         // 3. evaluation, selection, mutation, deposit
         reproduce<N, SW, TS, MODEL>(rec, w, p, a.rk, island, seg_lane, mask, g,
-                                    __ldg(&p.gen_sites[it]));
+                                    gen_site_at(p, it));
     }
     if constexpr (!kAtomic) {
         if (pending) st_release(flag, 1u);
@@ -434,7 +436,9 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_gen_kernel(const A
                               : md == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
             const uint32_t xn = md == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
                               : md == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
-            got = take128(a.mail + (static_cast<size_t>(yn * p.cols + xn) * 4u + (md ^ 1u)));
+            const uint32_t nb = yn * p.cols + xn;
+            if (in_bounds(nb < p.n_islands, p.status))
+                got = take128(a.mail + (static_cast<size_t>(nb) * 4u + (md ^ 1u)));
         }
     }
 
@@ -516,7 +520,7 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_gen_kernel(const A
         if (seg_lane >= 4u && seg_lane < 8u && out[1] != kNeverSent)
             refill128(a.mail + (static_cast<size_t>(island) * 4u + d), out);
     }
-    reproduce<N, 2, TS, MODEL>(rec, w, p, a.rk, island, seg_lane, mask, g, __ldg(&p.gen_sites[0]));
+    reproduce<N, 2, TS, MODEL>(rec, w, p, a.rk, island, seg_lane, mask, g, gen_site_at(p, 0u));
 #pragma unroll
     for (int ag = 0; ag < A; ++ag)
         p.dst[static_cast<size_t>(island) * N + seg_lane + 32u * ag] =

@@ -39,6 +39,7 @@ struct RunDesc {
     uint32_t theta_ben, theta_del, policy, log2_sites;
     uint32_t sites, bits, run_id, per_neighbor;
     uint32_t every_k, g, cur, pad;
+    int *status;  // the run's device status word
 };
 
 struct BatchArgs {
@@ -47,6 +48,8 @@ struct BatchArgs {
     const uint32_t *__restrict__ unit_local;  // block -> unit within the run
     const int32_t *__restrict__ sites;        // [run][chunk] curation sites of the chunk
     uint32_t chunk, dg;                       // chunk length, generation within the chunk
+    uint32_t n_runs;
+    int *status;                              // the batch's device status word
     RoundKeys rk;
 };
 
@@ -58,7 +61,8 @@ __global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
     __shared__ RunParams s_r;
     __shared__ uint32_t s_unit;
     if (threadIdx.x == 0) {
-        const uint32_t run = __ldg(&a.unit_run[blockIdx.x]);
+        uint32_t run = __ldg(&a.unit_run[blockIdx.x]);
+        if (!in_bounds(run < a.n_runs, a.status)) run = 0;
         const RunDesc &d = a.runs[run];
         const uint32_t cur = d.cur ^ (a.dg & 1u);
         s_r.src = d.pop[cur];
@@ -79,6 +83,8 @@ __global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
         s_r.migrate = d.per_neighbor && (d.every_k == 1u || s_r.g0 % d.every_k == 0u);
         s_r.gen_sites = a.sites + static_cast<size_t>(run) * a.chunk + a.dg;
         s_r.effect_scale = 1.0f;
+        s_r.gen_sites_left = a.chunk - a.dg;
+        s_r.status = d.status;
         s_unit = __ldg(&a.unit_local[blockIdx.x]);
     }
     __syncthreads();
@@ -191,6 +197,7 @@ struct ga_batch {
     cudaGraphExec_t graph = nullptr;
     uint32_t graph_chunk = 0;
     uint64_t launches = 0;
+    int *d_status = nullptr;  // device-check builds: failed index checks of the batch tables
 };
 
 namespace {
@@ -269,6 +276,7 @@ int rebuild(ga_batch *b)
         d.g = static_cast<uint32_t>(r->generation);
         d.cur = static_cast<uint32_t>(r->cur);
         d.pad = 0;
+        d.status = r->d_status;
     }
     if (cudaMalloc(&b->d_runs, n * sizeof(ga::RunDesc)) != cudaSuccess) return GA_ENOMEM;
     int rc = rc_of(cudaMemcpyAsync(b->d_runs, desc.data(), n * sizeof(ga::RunDesc),
@@ -343,6 +351,8 @@ int enqueue_chunk(ga_batch *b, uint32_t gens)
             a.sites = b->d_sites;
             a.chunk = gens;
             a.dg = dg;
+            a.n_runs = n;
+            a.status = b->d_status;
             a.rk = ga::round_keys(ga::Key{static_cast<uint32_t>(c.seed), static_cast<uint32_t>(c.seed >> 32)});
             k<<<c.units, c.warps * 32, 0, b->stream>>>(a);
             b->launches += 1;
@@ -437,6 +447,14 @@ int ga_batch_create(void *stream, ga_batch **out)
         }
         b->owns_stream = true;
     }
+    if (cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (b->d_status) cudaFree(b->d_status);
+        if (b->owns_stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return GA_ENOMEM;
+    }
     *out = b;
     return GA_OK;
 }
@@ -500,7 +518,18 @@ int ga_batch_step(ga_batch *b, uint32_t n_gens)
 int ga_batch_sync(ga_batch *b)
 {
     if (!b) return GA_EINVAL;
-    return rc_of(cudaStreamSynchronize(b->stream));
+    int rc = rc_of(cudaStreamSynchronize(b->stream));
+#if GA_DEVICE_CHECKS
+    // only device-check builds write the batch's status word
+    int st = GA_OK;
+    if (rc == GA_OK && cudaMemcpy(&st, b->d_status, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = GA_ECUDA;
+    if (rc == GA_OK && st != GA_OK) {
+        cudaMemset(b->d_status, 0, sizeof(int));
+        rc = st;
+    }
+#endif
+    return rc;
 }
 
 int ga_batch_launch_count(const ga_batch *b, uint64_t *launches)
@@ -610,6 +639,7 @@ int ga_batch_destroy(ga_batch *b)
     if (!b) return GA_EINVAL;
     int rc = rc_of(cudaStreamSynchronize(b->stream));
     free_device(b);
+    cudaFree(b->d_status);
     if (b->owns_stream) cudaStreamDestroy(b->stream);
     delete b;
     return rc;

@@ -4,7 +4,30 @@
 
 #include <cstdint>
 
+// Builds with device checks (libga_debug.so, -DGA_DEVICE_CHECKS=1) test the global-memory
+// indices of every kernel before use; a failed test records GA_EBOUNDS (-8) in the status
+// word it is given and the access is skipped.  In the normal build the tests compile away.
+#ifndef GA_DEVICE_CHECKS
+#define GA_DEVICE_CHECKS 0
+#endif
+
 namespace ga {
+
+// true when `ok`; otherwise (device-check builds only) records GA_EBOUNDS and returns false
+__device__ __forceinline__ bool in_bounds(bool ok, int *status)
+{
+#if GA_DEVICE_CHECKS
+    if (!ok) {
+        atomicCAS(status, 0, -8);
+        return false;
+    }
+    return true;
+#else
+    (void)ok;
+    (void)status;
+    return true;
+#endif
+}
 
 // Draw purposes, carried in the high half of the third Philox counter word.
 constexpr uint32_t kBirth = 1u;

@@ -39,7 +39,16 @@ struct RunParams {
     uint32_t g0, n_gens, migrate;           // migration (if set) happens at g0 only
     const int32_t *__restrict__ gen_sites;  // curation site of generation g0 + i
     float effect_scale;                     // fitness model: mutation amount scale
+    uint32_t gen_sites_left;                // entries of gen_sites from g0 on
+    int *status;                            // the run's device status word
 };
+
+// Curation site of generation g0 + it from the launch's site table (-1, no deposit, if a
+// device-check build finds `it` past the table).
+__device__ __forceinline__ int gen_site_at(const RunParams &p, uint32_t it)
+{
+    return in_bounds(it < p.gen_sites_left, p.status) ? __ldg(&p.gen_sites[it]) : -1;
+}
 
 // Candidate trait of slot `sel` of this lane's island.  For N <= 32 `sel` may carry extra
 // high bits: a shuffle of width N reads lane sel mod N, which is exactly the drawn slot.
@@ -175,7 +184,8 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
         const uint32_t c = child[ag][1];
         int site = gen_site;
         if (c != g) site = curation_site_of(p.policy, p.log2_sites, p.sites, c);
-        if (site >= 0) {
+        if (site >= 0 && in_bounds(static_cast<uint32_t>(site) < p.sites && site * p.bits < 32u * SW,
+                                   p.status)) {
             const uint32_t pos = static_cast<uint32_t>(site) * p.bits;
             const uint32_t wi = pos >> 5, sh = pos & 31u;
             const uint32_t m = ((1u << p.bits) - 1u) << sh;
@@ -236,9 +246,15 @@ __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &
                               : md == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
             const uint32_t xn = md == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
                               : md == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
-            const uint4 *srec = p.src + (static_cast<size_t>(yn * p.cols + xn) * N + e) * Q;
+            const uint32_t nb = yn * p.cols + xn;
+            const uint4 *srec = p.src + (static_cast<size_t>(nb) * N + e) * Q;
+            if (in_bounds(nb < p.n_islands && e < static_cast<uint32_t>(N), p.status)) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q) imm[q] = __ldg(&srec[q]);
+                for (int q = 0; q < Q; ++q) imm[q] = __ldg(&srec[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) imm[q] = make_uint4(0u, 0u, 0u, 0u);
+            }
         }
     }
 
@@ -311,14 +327,13 @@ __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &
             }
         }
     }
-    reproduce<N, SW, TS, MODEL>(rec, w, p, rk, island, seg_lane, mask, p.g0,
-                               __ldg(&p.gen_sites[0]));
+    reproduce<N, SW, TS, MODEL>(rec, w, p, rk, island, seg_lane, mask, p.g0, gen_site_at(p, 0u));
 
     // generations g0 + 1 .. g0 + n - 1: no migration, the island stays in registers
     for (uint32_t it = 1; it < p.n_gens; ++it) {
         birth_draws<N>(w, p, rk, p.g0 + it, island, seg_lane);
         reproduce<N, SW, TS, MODEL>(rec, w, p, rk, island, seg_lane, mask, p.g0 + it,
-                                    __ldg(&p.gen_sites[it]));
+                                    gen_site_at(p, it));
     }
 
 #pragma unroll

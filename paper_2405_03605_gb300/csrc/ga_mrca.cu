@@ -182,7 +182,7 @@ template <bool WIDE>
 __global__ void __launch_bounds__(kPairThreads)
 pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__restrict__ ranks_g,
             const uint32_t *__restrict__ meta, uint32_t log2_bits, uint32_t K, uint32_t T,
-            uint32_t *__restrict__ lo, uint32_t *__restrict__ hi)
+            uint32_t *__restrict__ lo, uint32_t *__restrict__ hi, int *__restrict__ status)
 {
     __shared__ uint32_t ranks[256];
     const uint32_t m = meta[0];
@@ -210,6 +210,7 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
     uint2 a0n = make_uint2(0u, 0u);
     uint4 a0 = make_uint4(0u, 0u, 0u, 0u), a1 = a0;
     for (;;) {
+        if (!in_bounds(i < j && j < n, status)) break;
         const uint32_t *pj = packed + static_cast<size_t>(j) * kPackWords;
         if (i != row) {
             const uint32_t *pi = packed + static_cast<size_t>(i) * kPackWords;
@@ -241,7 +242,8 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
             h = T;
             l = m >= K ? ranks[m - K] + 1u : 0u;
         } else {
-            const uint32_t istar = first_bit >> log2_bits;  // first mismatch, 0-based
+            uint32_t istar = first_bit >> log2_bits;  // first mismatch, 0-based
+            if (!in_bounds(istar < m, status)) istar = 0u;
             h = ranks[istar];
             l = istar >= K ? ranks[istar - K] + 1u : 0u;
         }
@@ -274,10 +276,10 @@ void launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, uint32_t 
     // sites * bits <= 64: every rank-ordered string fits in its first 64 bits
     if (sites * bits <= 64u)
         pair_kernel<false><<<grid, kPairThreads, 0, stream>>>(packed, n, ranks, meta, log2_bits,
-                                                               K, T, d_lo, d_hi);
+                                                               K, T, d_lo, d_hi, status);
     else
         pair_kernel<true><<<grid, kPairThreads, 0, stream>>>(packed, n, ranks, meta, log2_bits, K,
-                                                              T, d_lo, d_hi);
+                                                              T, d_lo, d_hi, status);
 }
 
 uint32_t margin(uint32_t bits)

@@ -145,6 +145,8 @@ RunParams run_params(const ga_run *run, const void *src, void *dst, uint32_t g0,
     r.migrate = migrate ? 1u : 0u;
     r.gen_sites = run->d_sites + (g0 - run->sites_base);
     r.effect_scale = static_cast<float>(run->cfg.effect_scale);
+    r.gen_sites_left = kSiteTableCap - static_cast<uint32_t>(g0 - run->sites_base);
+    r.status = run->d_status;
     return r;
 }
 

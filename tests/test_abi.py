@@ -102,6 +102,9 @@ def test_strerror(lib):
     from paper_2405_03605_gb300 import ga
     assert ga.strerror(0) == "ok"
     assert "invalid" in ga.strerror(-1)
+    for code in range(-8, 0):  # every GA_E* code of ga.h has its own message
+        assert ga.strerror(code) != "unknown error", code
+    assert "index check" in ga.strerror(-8)
     assert ga.strerror(-99) == "unknown error"
 
 

@@ -42,10 +42,13 @@
 // slot of the arrival from d (the partial Fisher-Yates draw of the synchronous mode, the
 // swap made whether or not anything arrives) and bits 8..15 for the member sent towards d.
 //
-// Mapping: one island per warp for N >= 32, 32/N islands per warp below; island lanes 0..3
-// take from the neighbours (lane d: direction d), lanes 4..7 own the island's send buffers
-// (lane 4 + d: towards d).  Every lane runs the window's generations back to back with its
-// agents in registers, as in the synchronous kernels.
+// Mapping (island_async_kernel): one island per warp for N >= 32, 32/N islands per warp
+// below; island lanes 0..3 take from the neighbours (lane d: direction d), lanes 4..7 own the
+// island's send buffers (lane 4 + d: towards d).  Every lane runs the window's generations
+// back to back with its agents in registers, as in the synchronous kernels.  Launches of a
+// single generation with 16-byte records use island_async_gen_kernel instead, whose block
+// shares the takes and landing draws of its islands like the synchronous kernel's migration
+// bookkeeping (described there).
 #include "ga_device.cuh"
 #include "ga_internal.h"
 #include "ga_island.cuh"

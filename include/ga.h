@@ -156,7 +156,7 @@ int ga_migrate_policy(ga_run *run, uint32_t per_neighbor, uint32_t every_k);
  * runs each window island by island in index order: a reproducible schedule the CPU model
  * follows exactly.  window in [1, GA_ASYNC_MAX_WINDOW]; the default after ga_create is 1.
  * Send buffers are emptied by ga_create, ga_reset and ga_load.  Asynchronous kernels exist
- * for island sizes 16, 32 and 64 (other sizes: GA_EUNSUPPORTED from ga_create).
+ * for island sizes 8 to 128 (4-agent islands: GA_EUNSUPPORTED from ga_create).
  * Errors: GA_EINVAL (window out of range), GA_ESTATE (run not in an asynchronous mode).
  */
 int ga_async_window(ga_run *run, uint32_t window);

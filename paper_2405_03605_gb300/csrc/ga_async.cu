@@ -535,7 +535,11 @@ using AsyncKernel = void (*)(AsyncArgs);
 template <int N, int TS>
 AsyncKernel pick_async_n(uint32_t surface_words, uint32_t model)
 {
-    if (model == GA_MODEL_FITNESS) return surface_words <= 2 ? island_async_kernel<N, 2, TS, 1> : nullptr;
+    if (model == GA_MODEL_FITNESS) {  // the float-fitness model: islands of 16 to 64 agents
+        if constexpr (N >= 16 && N <= 64)
+            return surface_words <= 2 ? island_async_kernel<N, 2, TS, 1> : nullptr;
+        return nullptr;
+    }
     if (surface_words <= 2) return island_async_kernel<N, 2, TS, 0>;
     if (surface_words <= 6) return island_async_kernel<N, 6, TS, 0>;
     if (surface_words <= 8) return island_async_kernel<N, 8, TS, 0>;
@@ -552,10 +556,12 @@ AsyncKernel pick_async_ts(uint32_t surface_words, uint32_t tsize, uint32_t model
 
 AsyncKernel pick_async(uint32_t island_size, uint32_t surface_words, uint32_t tsize, uint32_t model)
 {
-    switch (island_size) {
+    switch (island_size) {  // N >= 8: an island needs lanes 0..3 to take and 4..7 to send
+    case 8: return pick_async_ts<8>(surface_words, tsize, model);
     case 16: return pick_async_ts<16>(surface_words, tsize, model);
     case 32: return pick_async_ts<32>(surface_words, tsize, model);
     case 64: return pick_async_ts<64>(surface_words, tsize, model);
+    case 128: return pick_async_ts<128>(surface_words, tsize, model);
     default: return nullptr;
     }
 }
@@ -564,17 +570,22 @@ AsyncKernel pick_async(uint32_t island_size, uint32_t surface_words, uint32_t ts
 template <int N>
 AsyncKernel pick_async_gen_n(uint32_t tsize, uint32_t model)
 {
-    if (model == GA_MODEL_FITNESS)
-        return tsize == 5u ? island_async_gen_kernel<N, 5, 1> : island_async_gen_kernel<N, 0, 1>;
+    if (model == GA_MODEL_FITNESS) {
+        if constexpr (N >= 16 && N <= 64)
+            return tsize == 5u ? island_async_gen_kernel<N, 5, 1> : island_async_gen_kernel<N, 0, 1>;
+        return nullptr;
+    }
     return tsize == 5u ? island_async_gen_kernel<N, 5, 0> : island_async_gen_kernel<N, 0, 0>;
 }
 
 AsyncKernel pick_async_gen(uint32_t island_size, uint32_t tsize, uint32_t model)
 {
     switch (island_size) {
+    case 8: return pick_async_gen_n<8>(tsize, model);
     case 16: return pick_async_gen_n<16>(tsize, model);
     case 32: return pick_async_gen_n<32>(tsize, model);
     case 64: return pick_async_gen_n<64>(tsize, model);
+    case 128: return pick_async_gen_n<128>(tsize, model);
     default: return nullptr;
     }
 }

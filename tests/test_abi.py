@@ -52,21 +52,22 @@ def test_config_checks(lib):
 
 
 def test_async_config_checks(lib):
-    """Asynchronous modes: kernels for islands of 16, 32 and 64 agents, every record size
-    and both genome models; unknown modes are invalid."""
+    """Asynchronous modes: kernels for islands of 8 to 128 agents, every record size and
+    both genome models; unknown modes are invalid."""
     from paper_2405_03605_gb300 import ga
     from paper_2405_03605_gb300.workloads import SMALL_TORUS, ASYNC, ASYNC_SEQUENTIAL, \
         MODEL_FITNESS
     for mode in (ASYNC, ASYNC_SEQUENTIAL):
-        for n in (16, 32, 64):
+        for n in (8, 16, 32, 64, 128):
             for sites, bits in ((64, 1), (128, 1), (256, 1), (32, 8)):
                 shape = SMALL_TORUS.with_(mode=mode, island_size=n, surface_sites=sites,
                                           differentia_bits=bits)
                 assert ga.config_check(shape) == 0, (mode, n, sites, bits)
+            # the float-fitness model has kernels for 16, 32 and 64 agents in every mode
+            want = 0 if n in (16, 32, 64) else -6
             assert ga.config_check(SMALL_TORUS.with_(mode=mode, island_size=n,
-                                                     model=MODEL_FITNESS, p_del=0.33)) == 0
-        for n in (4, 8, 128):
-            assert ga.config_check(SMALL_TORUS.with_(mode=mode, island_size=n)) == -6
+                                                     model=MODEL_FITNESS, p_del=0.33)) == want
+        assert ga.config_check(SMALL_TORUS.with_(mode=mode, island_size=4)) == -6
     assert ga.config_check(SMALL_TORUS.with_(mode=3)) == -1
 
 

@@ -51,6 +51,11 @@ def _sequential_both(shape, calls):
     (1, 2, 32, 64, 1, STEADY, 1, 1, True),
     (2, 3, 64, 64, 1, TILTED, 1, 2, True),
     (4, 4, 32, 32, 2, HYBRID, 1, 1, True),
+    # 8- and 128-agent islands
+    (3, 4, 8, 64, 1, STEADY, 3, 1, True),
+    (3, 3, 8, 32, 8, TILTED, 1, 1, True),
+    (2, 3, 128, 64, 1, STEADY, 1, 1, True),
+    (2, 2, 128, 256, 1, STEADY, 4, 1, False),
 ])
 def test_sequential_matches_oracle(rows, cols, N, S, b, policy, window, every, drift):
     shape = RunShape(rows=rows, cols=cols, island_size=N, surface_sites=S, differentia_bits=b,
@@ -84,7 +89,7 @@ def test_sequential_tournament_sizes(tsize, N, window):
     assert_same(got, exp, N)
 
 
-@pytest.mark.parametrize("N", [16, 32, 64])
+@pytest.mark.parametrize("N", [8, 16, 32, 64, 128])
 def test_free_running_without_migration_is_sync(N):
     base = RunShape(rows=37, cols=41, island_size=N, migrate_every=0, seed=5, run_id=N)
     a = gpu_run(base.with_(mode=ASYNC, async_window=16))

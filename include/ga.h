@@ -249,7 +249,7 @@ typedef struct ga_batch ga_batch;
 int ga_batch_create(void *stream, ga_batch **out);
 
 /* Add a run (synchronises the run's stream and the batch's stream).  GA_EINVAL if it is
-   already a member. */
+   already a member of this or another batch. */
 int ga_batch_add(ga_batch *batch, ga_run *run);
 
 /* Remove a member run (synchronises the batch's stream; the run keeps its state). */
@@ -281,7 +281,8 @@ int ga_batch_autotune(ga_batch *batch, uint32_t trial_gens, uint32_t *chosen_chu
 int ga_batch_class_warps(const ga_batch *batch, uint32_t index, uint32_t *island_size,
                          uint32_t *warps);
 
-/* Destroy the batch (synchronises its stream; member runs are left intact). */
+/* Destroy the batch (synchronises its stream; member runs are left intact and belong to no
+   batch afterwards). */
 int ga_batch_destroy(ga_batch *batch);
 
 /*
@@ -324,7 +325,8 @@ int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_bytes, uint32_
                            uint32_t generation, const uint32_t *d_agent_ids, uint32_t n,
                            uint32_t *d_lo, uint32_t *d_hi, void *stream);
 
-/* Destroy the run (synchronises its stream; frees library-owned memory). */
+/* Destroy the run (synchronises its stream; frees library-owned memory).  A member of a
+   batch is first removed from it, as by ga_batch_remove. */
 int ga_destroy(ga_run *run);
 
 /* Static description of an error code. */

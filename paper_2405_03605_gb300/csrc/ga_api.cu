@@ -234,6 +234,7 @@ int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_
     run->cur = 0;
     run->mail = nullptr;
     run->async_window = 1;
+    run->batch = nullptr;
     if (cfg->mode != GA_SYNC) run->mail = base + ga::kHeaderBytes + 2 * buffer_stride(cfg);
     rc = cuda_rc(cudaMemsetAsync(base, 0, ga::kHeaderBytes, run->stream));
     if (rc == GA_OK) rc = clear_async_state(run);
@@ -406,7 +407,9 @@ int ga_curation_sites(uint32_t policy, uint32_t surface_sites, uint32_t t0, uint
 int ga_destroy(ga_run *run)
 {
     if (!run) return GA_EINVAL;
-    int rc = cuda_rc(cudaStreamSynchronize(run->stream));
+    int rc = GA_OK;
+    if (run->batch) rc = ga_batch_remove(run->batch, run);
+    if (cudaStreamSynchronize(run->stream) != cudaSuccess) rc = GA_ECUDA;
     if (run->owns_workspace && cudaFree(run->workspace) != cudaSuccess) rc = GA_ECUDA;
     delete run;
     return rc;

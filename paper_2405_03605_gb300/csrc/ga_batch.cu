@@ -462,13 +462,14 @@ int ga_batch_create(void *stream, ga_batch **out)
 int ga_batch_add(ga_batch *b, ga_run *run)
 {
     if (!b || !run) return GA_EINVAL;
-    if (std::find(b->runs.begin(), b->runs.end(), run) != b->runs.end()) return GA_EINVAL;
+    if (run->batch) return GA_EINVAL;  // already a member of this or another batch
 
     if (run->generation + 1 > 0xFFFFFFFFull) return GA_EINVAL;
     // the run's own queued work must be done before the batch stream touches its buffers
     if (cudaStreamSynchronize(run->stream) != cudaSuccess) return GA_ECUDA;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return GA_ECUDA;
     b->runs.push_back(run);
+    run->batch = b;
     b->dirty = true;
     return GA_OK;
 }
@@ -478,10 +479,12 @@ int ga_batch_remove(ga_batch *b, ga_run *run)
     if (!b || !run) return GA_EINVAL;
     auto it = std::find(b->runs.begin(), b->runs.end(), run);
     if (it == b->runs.end()) return GA_EINVAL;
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return GA_ECUDA;
+    // the run leaves the batch even when the wait fails, so that it can still be destroyed
+    const int rc = rc_of(cudaStreamSynchronize(b->stream));
     b->runs.erase(it);
+    run->batch = nullptr;
     b->dirty = true;
-    return GA_OK;
+    return rc;
 }
 
 int ga_batch_size(const ga_batch *b, uint32_t *n_runs)
@@ -638,6 +641,7 @@ int ga_batch_destroy(ga_batch *b)
 {
     if (!b) return GA_EINVAL;
     int rc = rc_of(cudaStreamSynchronize(b->stream));
+    for (ga_run *r : b->runs) r->batch = nullptr;
     free_device(b);
     cudaFree(b->d_status);
     if (b->owns_stream) cudaStreamDestroy(b->stream);

@@ -32,6 +32,7 @@ struct ga_run {
     // asynchronous modes only (null otherwise)
     uint8_t *mail;       // [island][direction] send buffers
     uint32_t async_window;
+    ga_batch *batch;     // the batch this run belongs to, if any
 };
 
 namespace ga {

@@ -1,5 +1,7 @@
 """Batched stepping (many runs per launch) is bit-identical to stepping each run alone and
 to the CPU oracle; autotuning changes no result."""
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -70,6 +72,39 @@ def test_batch_membership_changes():
         runs[i].sync()
         assert np.array_equal(runs[i].snapshot(), alone.snapshot()), i
     batch.close()
+
+
+def test_membership_rules():
+    """A run belongs to at most one batch; destroying a member removes it from its batch, so
+    the batch never steps a freed run; a destroyed batch leaves its runs free to join another."""
+    from paper_2405_03605_gb300 import ga
+    shapes = mixed_shapes()[:3]
+    runs = [gpu_run(s) for s in shapes]
+    b1 = ga.Batch(runs[:2])
+    b2 = ga.Batch()
+    with pytest.raises(ga.GaError):
+        b2.add(runs[0])              # member of b1
+    with pytest.raises(ga.GaError):
+        b1.add(runs[1])              # already in b1
+    b1.step(4)
+    b1.sync()
+    runs[1].close()                  # leaves b1 on destruction
+    n = C.c_uint32()
+    assert runs[0].lib.ga_batch_size(b1._h, C.byref(n)) == 0 and n.value == 1
+    b1.step(3)                       # steps the remaining member only
+    b1.sync()
+    assert runs[0].generation == 7
+    b1.close()
+    b2.add(runs[0])                  # free again once b1 is gone
+    b2.add(runs[2])
+    b2.step(2)
+    b2.sync()
+    assert runs[0].generation == 9 and runs[2].generation == 2
+    alone = gpu_run(shapes[0])
+    alone.step(9)
+    alone.sync()
+    assert np.array_equal(runs[0].snapshot(), alone.snapshot())
+    b2.close()
 
 
 def test_autotune_changes_no_result():

@@ -109,16 +109,17 @@ StepKernel pick_kernel(uint32_t island_size, uint32_t surface_words, uint32_t ts
     }
 }
 
+// SM count of the current device, read once (a function-local static: initialised once even
+// when handles are used from several threads).
 uint32_t sm_count()
 {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
+    static const uint32_t sms = [] {
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return static_cast<uint32_t>(sms);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? static_cast<uint32_t>(n) : 1u;
+    }();
+    return sms;
 }
 
 }  // namespace

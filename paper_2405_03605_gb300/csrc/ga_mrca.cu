@@ -176,25 +176,39 @@ __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_wo
 // steps 32 pairs at a time, carrying into the next rows when j passes n - 1, and reloads row
 // i's string only when i changes.  Pair indices fit 32 bits (n <= 65536: fewer than 2^31
 // pairs).  The first set bit of packed[i] ^ packed[j] gives the first mismatching rank index
-// i*.  WIDE: the rank-ordered strings need more than 64 bits (otherwise one 64-bit word
-// decides).
+// i*.  With 0-based sorted ranks r_0 < ... < r_{m-1}, a mismatch at index i* gives
+// hi = r_{i*}, lo = r_{i*-K} + 1 (0 if i* < K), and no mismatch hi = T, lo = r_{m-K} + 1.
+// 64-bit strings (S*b <= 64): the bits past m*b are zero in every string, so "no mismatch"
+// reads as i* = m, and one shared table holds both bounds for every i* in [0, m]:
+// tab[r] = (r >= K ? r_{r-K} + 1 : 0, r < m ? r_r : T).  WIDE strings (more than 64 bits)
+// take the first nonzero word of the XOR and the two rules separately (measured faster for
+// them than the table).
 template <bool WIDE>
 __global__ void __launch_bounds__(kPairThreads)
 pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__restrict__ ranks_g,
             const uint32_t *__restrict__ meta, uint32_t log2_bits, uint32_t K, uint32_t T,
-            uint32_t *__restrict__ lo, uint32_t *__restrict__ hi, int *__restrict__ status)
+            uint32_t per_warp, uint32_t *__restrict__ lo, uint32_t *__restrict__ hi,
+            int *__restrict__ status)
 {
-    __shared__ uint32_t ranks[256];
+    __shared__ uint2 tab[WIDE ? 1 : 257];
+    __shared__ uint32_t ranks[WIDE ? 256 : 1];
     const uint32_t m = meta[0];
-    for (uint32_t r = threadIdx.x; r < m; r += blockDim.x) ranks[r] = ranks_g[r];
+    if constexpr (!WIDE) {
+        for (uint32_t r = threadIdx.x; r <= m; r += blockDim.x)
+            tab[r] = make_uint2(r >= K ? ranks_g[r - K] + 1u : 0u, r < m ? ranks_g[r] : T);
+    } else {
+        for (uint32_t r = threadIdx.x; r < m; r += blockDim.x) ranks[r] = ranks_g[r];
+    }
     __syncthreads();
-    const unsigned long long n_pairs = static_cast<unsigned long long>(n) * (n - 1u) / 2ull;
-    const unsigned long long n_warps = static_cast<unsigned long long>(gridDim.x) * (kPairThreads / 32);
-    const unsigned long long per_warp = ((n_pairs + n_warps - 1ull) / n_warps + 31ull) / 32ull * 32ull;
-    const unsigned long long warp = (static_cast<unsigned long long>(blockIdx.x) * kPairThreads + threadIdx.x) >> 5;
-    unsigned long long p = warp * per_warp + (threadIdx.x & 31u);
-    const unsigned long long p_end = (warp + 1ull) * per_warp < n_pairs ? (warp + 1ull) * per_warp : n_pairs;
-    if (p >= p_end) return;
+    // pairs [warp * per_warp, (warp + 1) * per_warp) of n (n - 1) / 2 (per_warp: a multiple of
+    // 32 chosen on the host so that the grid covers every pair)
+    const uint32_t n_pairs = n * (n - 1u) / 2u;
+    const uint32_t warp = (blockIdx.x * kPairThreads + threadIdx.x) >> 5;
+    const unsigned long long w_end = static_cast<unsigned long long>(warp + 1u) * per_warp;
+    const uint32_t p_end = w_end < n_pairs ? static_cast<uint32_t>(w_end) : n_pairs;
+    const unsigned long long p0 = static_cast<unsigned long long>(warp) * per_warp + (threadIdx.x & 31u);
+    if (p0 >= p_end) return;
+    const uint32_t p = static_cast<uint32_t>(p0);
 
     const unsigned long long b = 2ull * n - 1ull;  // off(r) = r (b - r) / 2
     const float est = (static_cast<float>(b) - sqrtf(static_cast<float>(b * b - 8ull * p))) * 0.5f;
@@ -203,54 +217,61 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
     while (i > 0u && static_cast<unsigned long long>(i) * (b - i) / 2ull > p) --i;
     while (i + 2u < n && static_cast<unsigned long long>(i + 1u) * (b - i - 1u) / 2ull <= p) ++i;
     uint32_t j = i + 1u + static_cast<uint32_t>(p - static_cast<unsigned long long>(i) * (b - i) / 2ull);
-    uint32_t q = static_cast<uint32_t>(p);
-    const uint32_t q_end = static_cast<uint32_t>(p_end);
+    uint32_t q = p;
+    const uint32_t q_end = p_end;
+    uint32_t *lo_q = lo + q;
+    uint32_t *hi_q = hi + q;
 
-    uint32_t row = 0xFFFFFFFFu;  // row whose string a0 (, a1) holds
-    uint2 a0n = make_uint2(0u, 0u);
+    uint32_t row = 0xFFFFFFFFu;  // row whose string a0n (or a0, a1) holds
+    unsigned long long a0n = 0ull;
     uint4 a0 = make_uint4(0u, 0u, 0u, 0u), a1 = a0;
     for (;;) {
         if (!in_bounds(i < j && j < n, status)) break;
-        const uint32_t *pj = packed + static_cast<size_t>(j) * kPackWords;
         if (i != row) {
-            const uint32_t *pi = packed + static_cast<size_t>(i) * kPackWords;
             if constexpr (!WIDE) {
-                a0n = __ldg(reinterpret_cast<const uint2 *>(pi));
+                a0n = __ldg(reinterpret_cast<const unsigned long long *>(packed) + i * (kPackWords / 2u));
             } else {
-                a0 = __ldg(reinterpret_cast<const uint4 *>(pi));
-                a1 = __ldg(reinterpret_cast<const uint4 *>(pi) + 1);
+                a0 = __ldg(reinterpret_cast<const uint4 *>(packed) + i * (kPackWords / 4u));
+                a1 = __ldg(reinterpret_cast<const uint4 *>(packed) + i * (kPackWords / 4u) + 1u);
             }
             row = i;
         }
-        uint32_t first_bit = 0xFFFFFFFFu;
         if constexpr (!WIDE) {
-            const uint2 b0 = __ldg(reinterpret_cast<const uint2 *>(pj));
             const unsigned long long x =
-                (static_cast<unsigned long long>(b0.y ^ a0n.y) << 32) | (b0.x ^ a0n.x);
-            if (x != 0ull) first_bit = static_cast<uint32_t>(__ffsll(static_cast<long long>(x)) - 1);
+                __ldg(reinterpret_cast<const unsigned long long *>(packed) + j * (kPackWords / 2u)) ^ a0n;
+            // first differing bit, 64 if none
+            const uint32_t first_bit = static_cast<uint32_t>(__clzll(static_cast<long long>(__brevll(x))));
+            uint32_t istar = first_bit >> log2_bits;
+            istar = istar < m ? istar : m;
+            const uint2 bound = tab[istar];
+            __stcs(lo_q, bound.x);
+            __stcs(hi_q, bound.y);
         } else {
-            const uint4 b0 = __ldg(reinterpret_cast<const uint4 *>(pj));
-            const uint4 b1 = __ldg(reinterpret_cast<const uint4 *>(pj) + 1);
+            const uint4 b0 = __ldg(reinterpret_cast<const uint4 *>(packed) + j * (kPackWords / 4u));
+            const uint4 b1 = __ldg(reinterpret_cast<const uint4 *>(packed) + j * (kPackWords / 4u) + 1u);
             const uint32_t x[kPackWords] = {b0.x ^ a0.x, b0.y ^ a0.y, b0.z ^ a0.z, b0.w ^ a0.w,
                                             b1.x ^ a1.x, b1.y ^ a1.y, b1.z ^ a1.z, b1.w ^ a1.w};
+            uint32_t first_bit = 0xFFFFFFFFu;
 #pragma unroll
             for (int w = kPackWords - 1; w >= 0; --w)
                 if (x[w] != 0u) first_bit = 32u * w + (__ffs(x[w]) - 1u);
+            uint32_t l, h;
+            if (first_bit == 0xFFFFFFFFu) {
+                h = T;
+                l = m >= K ? ranks[m - K] + 1u : 0u;
+            } else {
+                uint32_t istar = first_bit >> log2_bits;  // first mismatch, 0-based
+                if (!in_bounds(istar < m, status)) istar = 0u;
+                h = ranks[istar];
+                l = istar >= K ? ranks[istar - K] + 1u : 0u;
+            }
+            __stcs(lo_q, l);
+            __stcs(hi_q, h);
         }
-        uint32_t l, h;
-        if (first_bit == 0xFFFFFFFFu) {
-            h = T;
-            l = m >= K ? ranks[m - K] + 1u : 0u;
-        } else {
-            uint32_t istar = first_bit >> log2_bits;  // first mismatch, 0-based
-            if (!in_bounds(istar < m, status)) istar = 0u;
-            h = ranks[istar];
-            l = istar >= K ? ranks[istar - K] + 1u : 0u;
-        }
-        __stcs(&lo[q], l);
-        __stcs(&hi[q], h);
         q += 32u;
         if (q >= q_end) break;
+        lo_q += 32;
+        hi_q += 32;
         j += 32u;
         while (j >= n) {  // past the end of row i: pair (i + 1, i + 2) follows (i, n - 1)
             j = j - n + i + 2u;
@@ -272,14 +293,17 @@ void launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, uint32_t 
     const unsigned long long pairs = static_cast<unsigned long long>(n) * (n - 1u) / 2ull;
     const unsigned long long want = (pairs + kPairThreads - 1) / kPairThreads;
     const uint32_t grid = static_cast<uint32_t>(want < kPairGrid ? want : kPairGrid);
+    const unsigned long long n_warps = static_cast<unsigned long long>(grid) * (kPairThreads / 32);
+    const uint32_t per_warp =
+        static_cast<uint32_t>(((pairs + n_warps - 1ull) / n_warps + 31ull) / 32ull * 32ull);
     const uint32_t log2_bits = bits == 1u ? 0u : bits == 2u ? 1u : bits == 4u ? 2u : 3u;
     // sites * bits <= 64: every rank-ordered string fits in its first 64 bits
     if (sites * bits <= 64u)
         pair_kernel<false><<<grid, kPairThreads, 0, stream>>>(packed, n, ranks, meta, log2_bits,
-                                                               K, T, d_lo, d_hi, status);
+                                                               K, T, per_warp, d_lo, d_hi, status);
     else
         pair_kernel<true><<<grid, kPairThreads, 0, stream>>>(packed, n, ranks, meta, log2_bits, K,
-                                                              T, d_lo, d_hi, status);
+                                                              T, per_warp, d_lo, d_hi, status);
 }
 
 uint32_t margin(uint32_t bits)

@@ -28,6 +28,31 @@ constexpr uint32_t kPackWords = 8;  // 256-bit rank-ordered strings
 constexpr int kPairThreads = 256;
 constexpr unsigned long long kPairGrid = 152ull * 8ull;  // 8 resident blocks on each of 152 SMs
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while the kernel before it on the stream is still running; it does the part of its
+// work that needs nothing from that kernel, then waits here (a hardware wait for the previous
+// grid's completion and memory flush; a no-op for a kernel launched without the attribute).
+__device__ __forceinline__ void wait_previous_grid() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+// Lets the next programmatically dependent kernel on the stream be scheduled now.
+__device__ __forceinline__ void release_next_grid() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... P, typename... A>
+cudaError_t launch_dependent(void (*kernel)(P...), unsigned grid, unsigned block,
+                             cudaStream_t stream, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 struct MrcaLayout {
     uint32_t *holder;  // [S]  rank + 1 held by each site (0: none)
     uint32_t *order;   // [S]  sites sorted by rank
@@ -71,6 +96,7 @@ __global__ void order_kernel(const uint32_t *__restrict__ holder, uint32_t *__re
                              uint32_t sites)
 {
     __shared__ uint32_t h[256];
+    release_next_grid();  // the pack kernel may start loading its agents' records
     const uint32_t k = threadIdx.x;
     const uint32_t mine = k < sites ? holder[k] : 0u;
     h[k] = mine;
@@ -94,6 +120,7 @@ rank_order_kernel(uint32_t *__restrict__ order, uint32_t *__restrict__ ranks,
                   uint32_t sites, uint32_t T)
 {
     __shared__ uint32_t h[256];
+    release_next_grid();  // the pack kernel may start loading its agents' records
     const uint32_t k = threadIdx.x;
     if (k < 256u) h[k] = 0u;
     __syncthreads();
@@ -140,20 +167,25 @@ __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_wo
                             int *__restrict__ status)
 {
     __shared__ uint32_t ord[256];
+    release_next_grid();  // the pair kernel may start its index set-up
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // the agent's record does not depend on the rank order: load it before waiting for it
+    const uint32_t id = a < n ? ids[a] : 0u;
+    const bool ok = a < n && id < n_agents;
+    const uint32_t *rec = pop + static_cast<size_t>(ok ? id : 0u) * record_words;
+    const uint32_t counter = ok ? rec[1] : T;
+    const uint32_t surf = (ok && lane < kPackWords && 2u + lane < record_words) ? rec[2 + lane] : 0u;
+    wait_previous_grid();
     const uint32_t m = meta[0];
     for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ord[i] = order[i];
     __syncthreads();
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (a >= n) return;  // whole warps
-    const uint32_t id = ids[a];
     uint32_t word_out = 0;
-    if (id >= n_agents) {
+    if (!ok) {
         if (lane == 0) atomicCAS(status, GA_OK, GA_EINVAL);
     } else {
-        const uint32_t *rec = pop + static_cast<size_t>(id) * record_words;
-        if (lane == 0 && rec[1] != T) atomicCAS(status, GA_OK, GA_ESTATE);
-        const uint32_t surf = (lane < kPackWords && 2u + lane < record_words) ? rec[2 + lane] : 0u;
+        if (lane == 0 && counter != T) atomicCAS(status, GA_OK, GA_ESTATE);
         const uint32_t per = 32u / bits, mask = (1u << bits) - 1u;
         const uint32_t pw = (m * bits + 31u) >> 5;
         for (uint32_t w = 0; w < pw; ++w) {
@@ -192,14 +224,6 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
 {
     __shared__ uint2 tab[WIDE ? 1 : 257];
     __shared__ uint32_t ranks[WIDE ? 256 : 1];
-    const uint32_t m = meta[0];
-    if constexpr (!WIDE) {
-        for (uint32_t r = threadIdx.x; r <= m; r += blockDim.x)
-            tab[r] = make_uint2(r >= K ? ranks_g[r - K] + 1u : 0u, r < m ? ranks_g[r] : T);
-    } else {
-        for (uint32_t r = threadIdx.x; r < m; r += blockDim.x) ranks[r] = ranks_g[r];
-    }
-    __syncthreads();
     // pairs [warp * per_warp, (warp + 1) * per_warp) of n (n - 1) / 2 (per_warp: a multiple of
     // 32 chosen on the host so that the grid covers every pair)
     const uint32_t n_pairs = n * (n - 1u) / 2u;
@@ -207,8 +231,8 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
     const unsigned long long w_end = static_cast<unsigned long long>(warp + 1u) * per_warp;
     const uint32_t p_end = w_end < n_pairs ? static_cast<uint32_t>(w_end) : n_pairs;
     const unsigned long long p0 = static_cast<unsigned long long>(warp) * per_warp + (threadIdx.x & 31u);
-    if (p0 >= p_end) return;
-    const uint32_t p = static_cast<uint32_t>(p0);
+    const bool active = p0 < p_end;
+    const uint32_t p = active ? static_cast<uint32_t>(p0) : 0u;
 
     const unsigned long long b = 2ull * n - 1ull;  // off(r) = r (b - r) / 2
     const float est = (static_cast<float>(b) - sqrtf(static_cast<float>(b * b - 8ull * p))) * 0.5f;
@@ -221,6 +245,18 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
     const uint32_t q_end = p_end;
     uint32_t *lo_q = lo + q;
     uint32_t *hi_q = hi + q;
+
+    // the rank table and the packed strings come from the kernels before this one
+    wait_previous_grid();
+    const uint32_t m = meta[0];
+    if constexpr (!WIDE) {
+        for (uint32_t r = threadIdx.x; r <= m; r += blockDim.x)
+            tab[r] = make_uint2(r >= K ? ranks_g[r - K] + 1u : 0u, r < m ? ranks_g[r] : T);
+    } else {
+        for (uint32_t r = threadIdx.x; r < m; r += blockDim.x) ranks[r] = ranks_g[r];
+    }
+    __syncthreads();
+    if (!active) return;
 
     uint32_t row = 0xFFFFFFFFu;  // row whose string a0n (or a0, a1) holds
     unsigned long long a0n = 0ull;
@@ -280,15 +316,19 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
     }
 }
 
-// pack + pair launches shared by the allocating and the fixed-scratch entry points
-void launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, uint32_t n_agents,
+// pack + pair launches shared by the allocating and the fixed-scratch entry points; both are
+// programmatically dependent launches (each starts its independent set-up while the kernel
+// before it finishes)
+cudaError_t launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, uint32_t n_agents,
                            const uint32_t *d_ids, uint32_t n, const uint32_t *order,
                            const uint32_t *ranks, const uint32_t *meta, uint32_t sites,
                            uint32_t bits, uint32_t K, uint32_t T, uint32_t *packed,
                            uint32_t *d_lo, uint32_t *d_hi, int *status, cudaStream_t stream)
 {
-    pack_kernel<<<(n + 7u) / 8u, 256, 0, stream>>>(pop, record_words, n_agents, d_ids, n, order,
-                                                   meta, bits, T, packed, status);
+    const cudaError_t e = launch_dependent(pack_kernel, (n + 7u) / 8u, 256, stream, pop,
+                                           record_words, n_agents, d_ids, n, order, meta, bits, T,
+                                           packed, status);
+    if (e != cudaSuccess) return e;
     // enough resident blocks for the whole GPU, each thread then sweeping several pairs
     const unsigned long long pairs = static_cast<unsigned long long>(n) * (n - 1u) / 2ull;
     const unsigned long long want = (pairs + kPairThreads - 1) / kPairThreads;
@@ -298,12 +338,9 @@ void launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, uint32_t 
         static_cast<uint32_t>(((pairs + n_warps - 1ull) / n_warps + 31ull) / 32ull * 32ull);
     const uint32_t log2_bits = bits == 1u ? 0u : bits == 2u ? 1u : bits == 4u ? 2u : 3u;
     // sites * bits <= 64: every rank-ordered string fits in its first 64 bits
-    if (sites * bits <= 64u)
-        pair_kernel<false><<<grid, kPairThreads, 0, stream>>>(packed, n, ranks, meta, log2_bits,
-                                                               K, T, per_warp, d_lo, d_hi, status);
-    else
-        pair_kernel<true><<<grid, kPairThreads, 0, stream>>>(packed, n, ranks, meta, log2_bits, K,
-                                                              T, per_warp, d_lo, d_hi, status);
+    return launch_dependent(sites * bits <= 64u ? pair_kernel<false> : pair_kernel<true>, grid,
+                            kPairThreads, stream, packed, n, ranks, meta, log2_bits, K, T, per_warp,
+                            d_lo, d_hi, status);
 }
 
 uint32_t margin(uint32_t bits)
@@ -526,10 +563,11 @@ cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t
                                        run->log2_sites, S, T, run->stream);
     if (made == 0) return cudaErrorUnknown;
     run->launches += made;
-    launch_pack_and_pairs(reinterpret_cast<const uint32_t *>(run->pop[run->cur]),
-                          run->record_bytes / 4u, run->n_agents, d_ids, n, l.order, l.ranks,
-                          l.meta, S, b, margin(b), T, l.packed, d_lo, d_hi, run->d_status,
-                          run->stream);
+    const cudaError_t e = launch_pack_and_pairs(
+        reinterpret_cast<const uint32_t *>(run->pop[run->cur]), run->record_bytes / 4u,
+        run->n_agents, d_ids, n, l.order, l.ranks, l.meta, S, b, margin(b), T, l.packed, d_lo,
+        d_hi, run->d_status, run->stream);
+    if (e != cudaSuccess) return e;
     run->launches += 2;
     return cudaGetLastError();
 }
@@ -617,10 +655,11 @@ extern "C" int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_byt
         launch_rank_order(l.holder, l.order, l.ranks, l.meta, curation, log2_sites, S,
                           generation, st) == 0)
         return GA_ECUDA;
-    launch_pack_and_pairs(static_cast<const uint32_t *>(d_records), record_bytes / 4u, n_agents,
-                          d_agent_ids, n, l.order, l.ranks, l.meta, S, b, margin(b), generation,
-                          l.packed, d_lo, d_hi, status, st);
-    if (cudaGetLastError() != cudaSuccess) return GA_ECUDA;
+    if (launch_pack_and_pairs(static_cast<const uint32_t *>(d_records), record_bytes / 4u,
+                              n_agents, d_agent_ids, n, l.order, l.ranks, l.meta, S, b, margin(b),
+                              generation, l.packed, d_lo, d_hi, status, st) != cudaSuccess ||
+        cudaGetLastError() != cudaSuccess)
+        return GA_ECUDA;
     int device_status = GA_OK;
     if (cudaMemcpyAsync(&device_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||

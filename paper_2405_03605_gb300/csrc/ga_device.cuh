@@ -29,6 +29,14 @@ __device__ __forceinline__ bool in_bounds(bool ok, int *status)
 #endif
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while the kernel before it on the stream is still running; it does the part of its
+// work that needs nothing from that kernel, then waits here (a hardware wait for the previous
+// grid's completion and memory flush; a no-op for a kernel launched without the attribute).
+__device__ __forceinline__ void wait_previous_grid() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+// Lets the next programmatically dependent kernel on the stream be scheduled now.
+__device__ __forceinline__ void release_next_grid() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // Draw purposes, carried in the high half of the third Philox counter word.
 constexpr uint32_t kBirth = 1u;
 constexpr uint32_t kFounder = 2u;

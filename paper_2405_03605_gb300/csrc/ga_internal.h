@@ -37,6 +37,25 @@ struct ga_run {
 
 namespace ga {
 
+// Launch `kernel` as a programmatic dependent of the previous kernel on `stream` (see
+// wait_previous_grid in ga_device.cuh).
+template <typename... P, typename... A>
+cudaError_t launch_dependent(void (*kernel)(P...), dim3 grid, dim3 block, cudaStream_t stream,
+                             A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 // Workspace header: the device status word (first 256 bytes), then the curation-site table
 // of the generations a ga_step call is about to run (one int32 per generation).
 constexpr size_t kStatusBytes = 256;

@@ -28,30 +28,6 @@ constexpr uint32_t kPackWords = 8;  // 256-bit rank-ordered strings
 constexpr int kPairThreads = 256;
 constexpr unsigned long long kPairGrid = 152ull * 8ull;  // 8 resident blocks on each of 152 SMs
 
-// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
-// start while the kernel before it on the stream is still running; it does the part of its
-// work that needs nothing from that kernel, then waits here (a hardware wait for the previous
-// grid's completion and memory flush; a no-op for a kernel launched without the attribute).
-__device__ __forceinline__ void wait_previous_grid() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
-// Lets the next programmatically dependent kernel on the stream be scheduled now.
-__device__ __forceinline__ void release_next_grid() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
-
-template <typename... P, typename... A>
-cudaError_t launch_dependent(void (*kernel)(P...), unsigned grid, unsigned block,
-                             cudaStream_t stream, A... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
-}
 
 struct MrcaLayout {
     uint32_t *holder;  // [S]  rank + 1 held by each site (0: none)

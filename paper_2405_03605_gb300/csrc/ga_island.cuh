@@ -214,8 +214,15 @@ __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &
     constexpr int BI = WARPS * P;           // islands per block
     constexpr int ML = BI * 4;                   // migration lanes: (island, direction)
 
-    __shared__ uint4 s_imm[ML][Q];                // immigrant records
-    __shared__ __align__(16) uint32_t s_slot[ML]; // landing slot of each immigrant
+    // Islands of at most 32 agents: each immigrant is written straight to its landing slot
+    // (s_in, indexed by island and slot) and a per-island mask marks the four slots that
+    // receive one, so an island lane tests one bit.  Larger islands: records and landing slots
+    // by (island, direction), each lane comparing its slot with the four.
+    constexpr bool kSlotTable = N <= 32;
+    __shared__ uint4 s_imm[kSlotTable ? 1 : ML][Q];                // by (island, direction)
+    __shared__ __align__(16) uint32_t s_slot[kSlotTable ? 1 : ML]; // landing slot of each
+    __shared__ uint4 s_in[kSlotTable ? BI * N : 1][Q];             // by (island, slot)
+    __shared__ uint32_t s_hit[kSlotTable ? BI : 1];                // bit s: slot s receives
 
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t seg_lane = lane % SEG;
@@ -297,17 +304,42 @@ __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &
                 if (static_cast<uint32_t>(dd) == md) slot = vr;
                 v[dd] = vd;
             }
-            s_slot[threadIdx.x] = slot;
-            if (island0 + (threadIdx.x >> 2) < p.n_islands) {
+            if constexpr (kSlotTable) {
+                const uint32_t li = threadIdx.x >> 2;  // the block's island of this lane
+                uint32_t bit = 1u << slot;
+                bit |= __shfl_xor_sync(mig_mask, bit, 1, 4);
+                bit |= __shfl_xor_sync(mig_mask, bit, 2, 4);
+                if (island0 + li < p.n_islands &&
+                    in_bounds(li * N + slot < static_cast<uint32_t>(BI * N), p.status)) {
 #pragma unroll
-                for (int q = 0; q < Q; ++q) s_imm[threadIdx.x][q] = imm[q];
+                    for (int q = 0; q < Q; ++q) s_in[li * N + slot][q] = imm[q];
+                }
+                if (md == 0u) s_hit[li] = bit;
+            } else {
+                s_slot[threadIdx.x] = slot;
+                if (island0 + (threadIdx.x >> 2) < p.n_islands) {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) s_imm[threadIdx.x][q] = imm[q];
+                }
             }
         }
         __syncthreads();
     }
     if (!valid) return;
 
-    if (p.migrate) {
+    if (p.migrate && kSlotTable) {
+        // the four immigrants land in their slots: every lane reads its slot's entry, the four
+        // receivers keep it
+        const bool hit = ((s_hit[local] >> seg_lane) & 1u) != 0u;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const uint4 xq = s_in[local * N + seg_lane][q];
+            const uint32_t w4[4] = {xq.x, xq.y, xq.z, xq.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (4 * q + k < LW) rec[0][4 * q + k] = hit ? w4[k] : rec[0][4 * q + k];
+        }
+    } else if (p.migrate) {
         // the four immigrants land in their slots
         const uint4 sl = *reinterpret_cast<const uint4 *>(&s_slot[4 * local]);
 #pragma unroll

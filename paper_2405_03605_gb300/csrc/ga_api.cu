@@ -227,6 +227,7 @@ int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_
     }
     uint8_t *base = static_cast<uint8_t *>(run->workspace);
     run->d_status = reinterpret_cast<int *>(base);
+    run->d_flag = reinterpret_cast<int *>(base + ga::kStatusBytes / 2);
     run->d_sites = reinterpret_cast<int32_t *>(base + ga::kStatusBytes);
     run->sites_base = 0;
     run->pop[0] = base + ga::kHeaderBytes;
@@ -235,6 +236,7 @@ int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_
     run->mail = nullptr;
     run->async_window = 1;
     run->batch = nullptr;
+    run->counters_uniform = true;
     if (cfg->mode != GA_SYNC) run->mail = base + ga::kHeaderBytes + 2 * buffer_stride(cfg);
     rc = cuda_rc(cudaMemsetAsync(base, 0, ga::kHeaderBytes, run->stream));
     if (rc == GA_OK) rc = clear_async_state(run);
@@ -253,6 +255,7 @@ int ga_reset(ga_run *run)
     if (!run) return GA_EINVAL;
     run->cur = 0;
     run->generation = 0;
+    run->counters_uniform = true;
     const int rc = clear_async_state(run);
     if (rc != GA_OK) return rc;
     return cuda_rc(ga::launch_founder(run, run->pop[0]));
@@ -340,8 +343,20 @@ int ga_load(ga_run *run, const void *host_src, size_t bytes, uint64_t generation
                         run->stream) != cudaSuccess)
         return GA_ECUDA;
     if (clear_async_state(run) != GA_OK) return GA_ECUDA;
+    // do all loaded counters equal the generation?  (synchronous steps then skip the
+    // closed-form curation path)
+    int mixed = 1;
+    if (run->cfg.mode == GA_SYNC) {
+        if (cudaMemsetAsync(run->d_flag, 0, sizeof(int), run->stream) != cudaSuccess ||
+            ga::launch_counter_check(run, static_cast<uint32_t>(generation), run->d_flag) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(&mixed, run->d_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                            run->stream) != cudaSuccess)
+            return GA_ECUDA;
+    }
     if (cudaStreamSynchronize(run->stream) != cudaSuccess) return GA_ECUDA;
     run->generation = generation;
+    run->counters_uniform = mixed == 0;
     return GA_OK;
 }
 

@@ -33,6 +33,8 @@ struct ga_run {
     uint8_t *mail;       // [island][direction] send buffers
     uint32_t async_window;
     ga_batch *batch;     // the batch this run belongs to, if any
+    bool counters_uniform;  // every agent's counter equals `generation` (founder, sync steps)
+    int *d_flag;         // device scratch word for ga_load's counter check (workspace header)
 };
 
 namespace ga {
@@ -69,6 +71,9 @@ constexpr uint32_t kMaxGensPerLaunch = 256;
 // `migrate`) happens only at g0.
 bool step_supported(uint32_t island_size, uint32_t surface_words, uint32_t model);
 cudaError_t launch_founder(ga_run *run, void *dst);
+// Set *d_flag to 1 if some agent of the current population has a counter other than
+// `generation` (the caller clears it first).
+cudaError_t launch_counter_check(ga_run *run, uint32_t generation, int *d_flag);
 cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t g0,
                                uint32_t n_gens, bool migrate, cudaStream_t stream);
 // Fill the site table with the curation sites of generations [g0, g0 + count).

@@ -97,10 +97,12 @@ static __device__ __noinline__ int curation_site_of(uint32_t policy, uint32_t lo
     return curation_site(policy, log2_sites, sites, T);
 }
 
-// g: the generation; gen_site: its curation site, valid for agents whose counter is g (all
-// agents in synchronous runs) -- any other counter takes the closed form.
+// g: the generation; gen_site: its curation site, valid for agents whose counter is g -- any
+// other counter takes the closed form.  CF = 0 compiles the closed form out: only for
+// launches in which every counter equals the generation (synchronous runs whose counters
+// were never loaded mixed), where it would never be taken.
 // MODEL 0: int32 trait, +1 / -1; MODEL 1: float fitness, -/+ effect_scale * |normal|.
-template <int N, int SW, int TS, int MODEL>
+template <int N, int SW, int TS, int MODEL, int CF = 1>
 __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
                                           const uint4 (&w)[Shape<N>::A], const RunParams &p,
                                           const RoundKeys &rk, uint32_t island, uint32_t seg_lane,
@@ -183,7 +185,9 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
 
         const uint32_t c = child[ag][1];
         int site = gen_site;
-        if (c != g) site = curation_site_of(p.policy, p.log2_sites, p.sites, c);
+        if constexpr (CF != 0) {
+            if (c != g) site = curation_site_of(p.policy, p.log2_sites, p.sites, c);
+        }
         if (site >= 0 && in_bounds(static_cast<uint32_t>(site) < p.sites && site * p.bits < 32u * SW,
                                    p.status)) {
             const uint32_t pos = static_cast<uint32_t>(site) * p.bits;
@@ -203,8 +207,9 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
 // One block's work: `unit` is the block's index within the run (islands
 // [unit * BI, unit * BI + BI)).  N: island size; SW: surface words carried per record (the
 // record is RW words); TS: the tournament size when fixed at compile time (0: read from the
-// run); WARPS: warps per block; MODEL: genome model (0 trait, 1 float fitness).
-template <int N, int SW, int TS, int WARPS, int MODEL = 0>
+// run); WARPS: warps per block; MODEL: genome model (0 trait, 1 float fitness); CF: closed-form
+// curation available (see reproduce).
+template <int N, int SW, int TS, int WARPS, int MODEL = 0, int CF = 1>
 __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &rk, uint32_t unit)
 {
     constexpr int A = Shape<N>::A, P = Shape<N>::P, SEG = Shape<N>::SEG;
@@ -359,13 +364,13 @@ __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &
             }
         }
     }
-    reproduce<N, SW, TS, MODEL>(rec, w, p, rk, island, seg_lane, mask, p.g0, gen_site_at(p, 0u));
+    reproduce<N, SW, TS, MODEL, CF>(rec, w, p, rk, island, seg_lane, mask, p.g0, gen_site_at(p, 0u));
 
     // generations g0 + 1 .. g0 + n - 1: no migration, the island stays in registers
     for (uint32_t it = 1; it < p.n_gens; ++it) {
         birth_draws<N>(w, p, rk, p.g0 + it, island, seg_lane);
-        reproduce<N, SW, TS, MODEL>(rec, w, p, rk, island, seg_lane, mask, p.g0 + it,
-                                    gen_site_at(p, it));
+        reproduce<N, SW, TS, MODEL, CF>(rec, w, p, rk, island, seg_lane, mask, p.g0 + it,
+                                        gen_site_at(p, it));
     }
 
 #pragma unroll

@@ -15,10 +15,10 @@ struct StepArgs {
     RoundKeys rk;
 };
 
-template <int N, int SW, int TS, int MODEL = 0>
+template <int N, int SW, int TS, int MODEL = 0, int CF = 1>
 __global__ void __launch_bounds__(kStepThreads) island_step_kernel(const StepArgs a)
 {
-    step_block<N, SW, TS, kStepWarps, MODEL>(a.r, a.rk, blockIdx.x);
+    step_block<N, SW, TS, kStepWarps, MODEL, CF>(a.r, a.rk, blockIdx.x);
 }
 
 // Every record becomes the founder: trait 0, counter 0, surface word w = word 0 of
@@ -44,6 +44,14 @@ __global__ void founder_kernel(uint4 *__restrict__ dst, uint32_t n_agents, uint3
         const uint32_t q = static_cast<uint32_t>(i % q_per_rec);
         dst[i] = make_uint4(words[4 * q], words[4 * q + 1], words[4 * q + 2], words[4 * q + 3]);
     }
+}
+
+__global__ void counter_check_kernel(const uint32_t *__restrict__ pop, uint32_t record_words,
+                                     uint32_t n_agents, uint32_t generation, int *__restrict__ flag)
+{
+    for (size_t a = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; a < n_agents;
+         a += static_cast<size_t>(gridDim.x) * blockDim.x)
+        if (pop[a * record_words + 1u] != generation) *flag = 1;  // every writer stores 1
 }
 
 __global__ void curation_sites_kernel(uint32_t policy, uint32_t log2_sites, uint32_t sites,
@@ -84,6 +92,21 @@ StepKernel pick_fitness(uint32_t surface_words, uint32_t tsize)
 {
     if (surface_words > 2) return nullptr;
     return tsize == 5 ? island_step_kernel<N, 2, 5, 1> : island_step_kernel<N, 2, 0, 1>;
+}
+
+// Kernels without the closed-form curation path, for launches whose counters all equal the
+// generation: 16-byte trait records, tournament size 5 (the paper's, Sec. 3).
+StepKernel pick_uniform(uint32_t island_size)
+{
+    switch (island_size) {
+    case 4: return island_step_kernel<4, 2, 5, 0, 0>;
+    case 8: return island_step_kernel<8, 2, 5, 0, 0>;
+    case 16: return island_step_kernel<16, 2, 5, 0, 0>;
+    case 32: return island_step_kernel<32, 2, 5, 0, 0>;
+    case 64: return island_step_kernel<64, 2, 5, 0, 0>;
+    case 128: return island_step_kernel<128, 2, 5, 0, 0>;
+    default: return nullptr;
+    }
 }
 
 StepKernel pick_kernel(uint32_t island_size, uint32_t surface_words, uint32_t tsize,
@@ -172,12 +195,29 @@ cudaError_t launch_founder(ga_run *run, void *dst)
     return cudaGetLastError();
 }
 
+cudaError_t launch_counter_check(ga_run *run, uint32_t generation, int *d_flag)
+{
+    size_t blocks = (static_cast<size_t>(run->n_agents) + 255) / 256;
+    const size_t cap = static_cast<size_t>(sm_count()) * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    counter_check_kernel<<<static_cast<unsigned>(blocks), 256, 0, run->stream>>>(
+        static_cast<const uint32_t *>(static_cast<const void *>(run->pop[run->cur])),
+        run->record_bytes / 4u, run->n_agents, generation, d_flag);
+    run->launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t g0,
                                uint32_t n_gens, bool migrate, cudaStream_t stream)
 {
+    const bool uniform = run->cfg.mode == GA_SYNC && run->counters_uniform &&
+                         run->cfg.model == GA_MODEL_TRAIT && run->surface_words <= 2 &&
+                         run->cfg.tournament_size == 5;
     const StepKernel k =
-        pick_kernel(run->cfg.island_size, run->surface_words, run->cfg.tournament_size,
-                    run->cfg.model);
+        uniform ? pick_uniform(run->cfg.island_size)
+                : pick_kernel(run->cfg.island_size, run->surface_words, run->cfg.tournament_size,
+                              run->cfg.model);
     if (!k) return cudaErrorInvalidValue;
     StepArgs a;
     a.r = run_params(run, src, dst, g0, n_gens, migrate);

@@ -145,6 +145,45 @@ def test_reset_and_resume():
     assert np.array_equal(a.snapshot(), full)
 
 
+@pytest.mark.parametrize("policy,S,b", [(STEADY, 64, 1), (TILTED, 32, 8), (HYBRID, 64, 1)])
+def test_sync_steps_from_mixed_counters(policy, S, b):
+    """A synchronous run loaded with agents of different counters (an asynchronous population)
+    deposits each agent at its own counter's site, alone and as a batch member."""
+    from paper_2405_03605_gb300 import ga
+    shape = RunShape(rows=4, cols=6, island_size=32, surface_sites=S, differentia_bits=b,
+                     curation=policy, seed=21)
+    src = oracle_for(shape)
+    src.step_async(60, window=7)
+    mixed = src.snapshot()
+    counters = mixed.view(np.uint32)[:, 1]
+    assert len(set(counters.tolist())) > 1
+    o = oracle_for(shape)
+    o.load(mixed, 60)
+    o.step(35)
+    exp = o.snapshot()
+    g = gpu_run(shape)
+    g.load(mixed, 60)
+    g.step(35)
+    g.sync()
+    assert_same(g.snapshot(), exp, shape.island_size)
+    h = gpu_run(shape)
+    h.load(mixed, 60)
+    batch = ga.Batch([h])
+    batch.step(35)
+    batch.sync()
+    assert_same(h.snapshot(), exp, shape.island_size)
+    batch.close()
+    # then loading a population whose counters all equal the generation (a synchronous run's)
+    # restores the uniform path
+    u = oracle_for(shape)
+    u.step(20)
+    g.load(u.snapshot(), 20)
+    g.step(10)
+    g.sync()
+    u.step(10)
+    assert_same(g.snapshot(), u.snapshot(), shape.island_size)
+
+
 def test_library_allocated_workspace():
     from paper_2405_03605_gb300 import ga
     shape = RunShape(rows=3, cols=3, seed=4)

@@ -134,31 +134,8 @@ struct AsyncArgs {
     uint32_t every_k;      // migration on generations g with g mod every_k == 0
     uint32_t phase0;       // g0 mod every_k
     uint32_t first, last;  // islands [first, last) run in this launch
-    uint32_t cols_m, cols_l;  // island / cols = multiply-shift (cols_l = 0: cols == 1)
 };
 
-// Unsigned division by the torus width as a multiply and shifts, with the magic number of
-// Granlund and Montgomery ("Division by invariant integers using multiplication", PLDI
-// 1994, the round-up method for a 32-bit divisor d >= 2): l = ceil(log2 d),
-// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> 1)) >> (l - 1) with t = umulhi(m, n).
-void division_magic(uint32_t d, uint32_t &m, uint32_t &l)
-{
-    if (d <= 1u) {
-        m = 0;
-        l = 0;
-        return;
-    }
-    l = 0;
-    while ((1ull << l) < d) ++l;
-    m = static_cast<uint32_t>((((1ull << 32) * ((1ull << l) - d)) / d) + 1ull);
-}
-
-__device__ __forceinline__ uint32_t div_cols(uint32_t n, uint32_t m, uint32_t l)
-{
-    if (l == 0u) return n;  // cols == 1
-    const uint32_t t = __umulhi(m, n);
-    return (t + ((n - t) >> 1)) >> (l - 1u);
-}
 
 // Send-buffer size in uint4 for a record of Q uint4.
 __host__ __device__ constexpr int box_words(int Q) { return Q == 1 ? 1 : 1 + Q; }
@@ -212,7 +189,7 @@ island_async_kernel(const AsyncArgs a)
     const bool sender = seg_lane >= 4u && seg_lane < 8u;
     uint4 *box = nullptr;
     if (taker) {
-        const uint32_t y = div_cols(island, a.cols_m, a.cols_l), x = island - y * p.cols;
+        const uint32_t y = div_cols(island, p.cols_m, p.cols_l), x = island - y * p.cols;
         const uint32_t yn = d == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
                           : d == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
         const uint32_t xn = d == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
@@ -434,7 +411,7 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_gen_kernel(const A
         if (isl < a.last) {
             const uint32_t u = philox_rk(g, isl, md | (kBirth << 16), p.run_id, a.rk).w;
             r = md + (((u >> 16) * static_cast<uint32_t>(N - md)) >> 16);
-            const uint32_t y = div_cols(isl, a.cols_m, a.cols_l), x = isl - y * p.cols;
+            const uint32_t y = div_cols(isl, p.cols_m, p.cols_l), x = isl - y * p.cols;
             const uint32_t yn = md == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
                               : md == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
             const uint32_t xn = md == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
@@ -640,7 +617,6 @@ cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_
     a.phase0 = g0 % run->every_k;
     a.first = first;
     a.last = last;
-    division_magic(run->cfg.cols, a.cols_m, a.cols_l);
     const uint32_t N = run->cfg.island_size;
     const uint32_t per_block = kAsyncWarps * (N >= 32 ? 1u : 32u / N);
     const uint32_t blocks = (last - first + per_block - 1) / per_block;

@@ -36,6 +36,7 @@ namespace {
 struct RunDesc {
     const uint4 *pop[2];
     uint32_t rows, cols, n_islands, tsize;
+    uint32_t cols_m, cols_l;  // island / cols as a multiply-shift
     uint32_t theta_ben, theta_del, policy, log2_sites;
     uint32_t sites, bits, run_id, per_neighbor;
     uint32_t every_k, g, cur, pad;
@@ -70,6 +71,8 @@ __global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
         s_r.rows = d.rows;
         s_r.cols = d.cols;
         s_r.n_islands = d.n_islands;
+        s_r.cols_m = d.cols_m;
+        s_r.cols_l = d.cols_l;
         s_r.tsize = d.tsize;
         s_r.theta_ben = d.theta_ben;
         s_r.theta_del = d.theta_del;
@@ -263,6 +266,7 @@ int rebuild(ga_batch *b)
         d.rows = r->cfg.rows;
         d.cols = r->cfg.cols;
         d.n_islands = r->n_islands;
+        ga::division_magic(r->cfg.cols, d.cols_m, d.cols_l);
         d.tsize = r->cfg.tournament_size;
         d.theta_ben = r->theta_ben;
         d.theta_del = r->theta_del;

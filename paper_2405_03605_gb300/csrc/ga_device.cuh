@@ -223,6 +223,29 @@ __device__ __forceinline__ int curation_site(uint32_t policy, uint32_t s, uint32
     return static_cast<int>(S >> 1) + tilted_site(S >> 1, T >> 1);
 }
 
+// Unsigned division by the torus width as a multiply and shifts, with the magic number of
+// Granlund and Montgomery ("Division by invariant integers using multiplication", PLDI
+// 1994, the round-up method for a 32-bit divisor d >= 2): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> 1)) >> (l - 1) with t = umulhi(m, n).
+inline void division_magic(uint32_t d, uint32_t &m, uint32_t &l)
+{
+    if (d <= 1u) {
+        m = 0;
+        l = 0;
+        return;
+    }
+    l = 0;
+    while ((1ull << l) < d) ++l;
+    m = static_cast<uint32_t>((((1ull << 32) * ((1ull << l) - d)) / d) + 1ull);
+}
+
+__device__ __forceinline__ uint32_t div_cols(uint32_t n, uint32_t m, uint32_t l)
+{
+    if (l == 0u) return n;  // cols == 1
+    const uint32_t t = __umulhi(m, n);
+    return (t + ((n - t) >> 1)) >> (l - 1u);
+}
+
 // ---------------------------------------------------------------------------------------
 // Torus neighbour of island (y, x) in direction d: 0 north, 1 south, 2 east, 3 west.
 // ---------------------------------------------------------------------------------------

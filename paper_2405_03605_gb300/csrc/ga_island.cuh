@@ -32,6 +32,7 @@ struct RunParams {
     const uint4 *__restrict__ src;          // records before generation g0
     uint4 *__restrict__ dst;                // records after generation g0 + n_gens - 1
     uint32_t rows, cols, n_islands;
+    uint32_t cols_m, cols_l;                // island / cols as a multiply-shift (div_cols)
     uint32_t tsize;
     uint32_t theta_ben, theta_del;
     uint32_t policy, log2_sites, sites, bits;
@@ -253,7 +254,7 @@ __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &
             const uint32_t u = philox_rk(p.g0, isl, md | (kBirth << 16), p.run_id, rk).w;
             r = md + (((u >> 16) * static_cast<uint32_t>(N - md)) >> 16);
             const uint32_t e = (((u >> 8) & 0xFFu) * N) >> 8;
-            const uint32_t y = isl / p.cols, x = isl - y * p.cols;
+            const uint32_t y = div_cols(isl, p.cols_m, p.cols_l), x = isl - y * p.cols;
             const uint32_t yn = md == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
                               : md == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
             const uint32_t xn = md == 2u ? (x + 1u == p.cols ? 0u : x + 1u)

@@ -156,6 +156,7 @@ RunParams run_params(const ga_run *run, const void *src, void *dst, uint32_t g0,
     r.rows = run->cfg.rows;
     r.cols = run->cfg.cols;
     r.n_islands = run->n_islands;
+    division_magic(run->cfg.cols, r.cols_m, r.cols_l);
     r.tsize = run->cfg.tournament_size;
     r.theta_ben = run->theta_ben;
     r.theta_del = run->theta_del;

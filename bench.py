@@ -147,11 +147,11 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
-# DRAM bytes (read + write) of one island_step_kernel<32,2,5> launch on the 512x1024x32 grid:
+# DRAM bytes (read + write) of one island_step_kernel<32,2,5,0,0> launch on the 512x1024x32 grid:
 # dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this kernel build, and
 # its warp-instructions per island-generation (smsp__inst_executed.sum / 524,288 islands).
-ISLAND_STEP_TRAFFIC = {"kernel": "island_step_kernel<32,2,5>", "bytes": 494.2e6,
-                       "inst_per_island_gen": 109.9e6 / 524288,
+ISLAND_STEP_TRAFFIC = {"kernel": "island_step_kernel<32,2,5,0,0>", "bytes": 494.5e6,
+                       "inst_per_island_gen": 98.63e6 / 524288,
                        "rows": 512, "cols": 1024, "island_size": 32}
 
 

@@ -54,7 +54,7 @@ struct BatchArgs {
     RoundKeys rk;
 };
 
-template <int N, int SW, int TS, int W>
+template <int N, int SW, int TS, int W, int CF = 1>
 __global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
 {
     // the block's run parameters, staged once in shared memory: the block body reads them
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
         s_unit = __ldg(&a.unit_local[blockIdx.x]);
     }
     __syncthreads();
-    step_block<N, SW, TS, W>(s_r, a.rk, s_unit);
+    step_block<N, SW, TS, W, 0, CF>(s_r, a.rk, s_unit);
 }
 
 __global__ void batch_sites_kernel(const RunDesc *__restrict__ runs, uint32_t n_runs,
@@ -117,40 +117,41 @@ __global__ void batch_advance_kernel(RunDesc *__restrict__ runs, uint32_t n_runs
 using BatchKernel = void (*)(BatchArgs);
 
 // Tournament size 5 (the paper's, Sec. 3) has its own instantiations; other sizes use the
-// kernels that read the size from the run.
-template <int N, int SW, int TS>
+// kernels that read the size from the run.  CF = 0: classes whose members' counters all equal
+// their generations, compiled without the closed-form curation path (16-byte records only).
+template <int N, int SW, int TS, int CF>
 BatchKernel pick_w(uint32_t warps)
 {
     switch (warps) {
-    case 4: return batch_step_kernel<N, SW, TS, 4>;
-    case 8: return batch_step_kernel<N, SW, TS, 8>;
-    case 16: return batch_step_kernel<N, SW, TS, 16>;
+    case 4: return batch_step_kernel<N, SW, TS, 4, CF>;
+    case 8: return batch_step_kernel<N, SW, TS, 8, CF>;
+    case 16: return batch_step_kernel<N, SW, TS, 16, CF>;
     default: return nullptr;
     }
 }
 
-template <int N, int SW>
+template <int N, int SW, int CF>
 BatchKernel pick_ts(uint32_t ts, uint32_t warps)
 {
-    return ts == 5 ? pick_w<N, SW, 5>(warps) : pick_w<N, SW, 0>(warps);
+    return ts == 5 ? pick_w<N, SW, 5, CF>(warps) : pick_w<N, SW, 0, CF>(warps);
 }
 
 template <int N>
-BatchKernel pick_sw(uint32_t sw, uint32_t ts, uint32_t warps)
+BatchKernel pick_sw(uint32_t sw, uint32_t ts, uint32_t warps, bool uniform)
 {
-    if (sw <= 2) return pick_ts<N, 2>(ts, warps);
-    if (sw <= 6) return pick_ts<N, 6>(ts, warps);
-    if (sw <= 8) return pick_ts<N, 8>(ts, warps);
+    if (sw <= 2) return uniform ? pick_ts<N, 2, 0>(ts, warps) : pick_ts<N, 2, 1>(ts, warps);
+    if (sw <= 6) return pick_ts<N, 6, 1>(ts, warps);
+    if (sw <= 8) return pick_ts<N, 8, 1>(ts, warps);
     return nullptr;
 }
 
-BatchKernel pick(uint32_t n, uint32_t sw, uint32_t ts, uint32_t warps)
+BatchKernel pick(uint32_t n, uint32_t sw, uint32_t ts, uint32_t warps, bool uniform = false)
 {
     switch (n) {
-    case 8: return pick_sw<8>(sw, ts, warps);
-    case 16: return pick_sw<16>(sw, ts, warps);
-    case 32: return pick_sw<32>(sw, ts, warps);
-    case 64: return pick_sw<64>(sw, ts, warps);
+    case 8: return pick_sw<8>(sw, ts, warps, uniform);
+    case 16: return pick_sw<16>(sw, ts, warps, uniform);
+    case 32: return pick_sw<32>(sw, ts, warps, uniform);
+    case 64: return pick_sw<64>(sw, ts, warps, uniform);
     default: return nullptr;
     }
 }
@@ -161,6 +162,7 @@ constexpr uint32_t kChunkChoices[] = {16, 64, 256};
 struct Class {
     uint32_t island_size, sw_class, ts_class;
     uint64_t seed;
+    bool uniform = false;  // every member's counters equal its generation (no closed form)
     uint32_t warps = 8;
     std::vector<uint32_t> members;  // indices into the batch's run list
     uint32_t *d_unit_run = nullptr, *d_unit_local = nullptr;
@@ -190,7 +192,8 @@ struct ga_batch {
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
     std::vector<ga_run *> runs;
-    std::vector<std::pair<uint64_t, int>> expect;  // members' (generation, cur) the device holds
+    // members' (generation, cur, counters uniform) as the device tables hold them
+    std::vector<std::tuple<uint64_t, int, bool>> expect;
     std::vector<ga::Class> classes;
     ga::RunDesc *d_runs = nullptr;
     int32_t *d_sites = nullptr;
@@ -227,16 +230,20 @@ void free_device(ga_batch *b)
 // (Re)build classes, descriptors and block tables after membership or tuning changes.
 int rebuild(ga_batch *b)
 {
-    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint64_t>, uint32_t> warps_of;
-    for (const auto &c : b->classes) warps_of[{c.island_size, c.sw_class, c.ts_class, c.seed}] = c.warps;
+    using Key = std::tuple<uint32_t, uint32_t, uint32_t, uint64_t, bool>;
+    std::map<Key, uint32_t> warps_of;
+    for (const auto &c : b->classes)
+        warps_of[{c.island_size, c.sw_class, c.ts_class, c.seed, c.uniform}] = c.warps;
     free_device(b);
     b->classes.clear();
-    std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint64_t>, size_t> index;
+    std::map<Key, size_t> index;
     for (uint32_t i = 0; i < b->runs.size(); ++i) {
         const ga_run *r = b->runs[i];
         if (ga::solo(r)) continue;
-        const auto key = std::make_tuple(r->cfg.island_size, ga::sw_class(r->surface_words),
-                                         ga::ts_class(r->cfg.tournament_size), r->cfg.seed);
+        const uint32_t swc = ga::sw_class(r->surface_words);
+        const Key key = std::make_tuple(r->cfg.island_size, swc,
+                                        ga::ts_class(r->cfg.tournament_size), r->cfg.seed,
+                                        swc == 2u && r->counters_uniform);
         auto it = index.find(key);
         if (it == index.end()) {
             ga::Class c;
@@ -244,6 +251,7 @@ int rebuild(ga_batch *b)
             c.sw_class = std::get<1>(key);
             c.ts_class = std::get<2>(key);
             c.seed = std::get<3>(key);
+            c.uniform = std::get<4>(key);
             auto w = warps_of.find(key);
             if (w != warps_of.end()) c.warps = w->second;
             index[key] = b->classes.size();
@@ -311,7 +319,7 @@ int rebuild(ga_batch *b)
     rc = rc_of(cudaStreamSynchronize(b->stream));  // host vectors above go out of scope
     if (rc != GA_OK) return rc;
     b->expect.clear();
-    for (const ga_run *r : b->runs) b->expect.emplace_back(r->generation, r->cur);
+    for (const ga_run *r : b->runs) b->expect.emplace_back(r->generation, r->cur, r->counters_uniform);
     b->dirty = false;
     return GA_OK;
 }
@@ -321,7 +329,8 @@ bool members_moved(const ga_batch *b)
 {
     if (b->expect.size() != b->runs.size()) return true;
     for (size_t i = 0; i < b->runs.size(); ++i)
-        if (b->expect[i].first != b->runs[i]->generation || b->expect[i].second != b->runs[i]->cur)
+        if (b->expect[i] != std::make_tuple(b->runs[i]->generation, b->runs[i]->cur,
+                                            b->runs[i]->counters_uniform))
             return true;
     return false;
 }
@@ -346,7 +355,8 @@ int enqueue_chunk(ga_batch *b, uint32_t gens)
     b->launches += 1;
     for (uint32_t dg = 0; dg < gens; ++dg) {
         for (const auto &c : b->classes) {
-            const ga::BatchKernel k = ga::pick(c.island_size, c.sw_class, c.ts_class, c.warps);
+            const ga::BatchKernel k =
+                ga::pick(c.island_size, c.sw_class, c.ts_class, c.warps, c.uniform);
             if (!k) return GA_EUNSUPPORTED;
             ga::BatchArgs a;
             a.runs = b->d_runs;
@@ -428,7 +438,7 @@ void advance_host(ga_batch *b, uint32_t n_gens)
             r->cur ^= static_cast<int>(n_gens & 1u);
             r->launches += n_gens;  // one island-step launch per generation covers each run
         }
-        b->expect[i] = {r->generation, r->cur};
+        b->expect[i] = std::make_tuple(r->generation, r->cur, r->counters_uniform);
     }
 }
 

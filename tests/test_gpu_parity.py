@@ -166,9 +166,14 @@ def test_sync_steps_from_mixed_counters(policy, S, b):
     g.step(35)
     g.sync()
     assert_same(g.snapshot(), exp, shape.island_size)
+    # a batch member first stepped in a uniform-counter class, then loaded with the mixed
+    # counters at the same generation and buffer: only its counters' uniformity changes, and
+    # the batch must move it to a class with the closed form
     h = gpu_run(shape)
-    h.load(mixed, 60)
     batch = ga.Batch([h])
+    batch.step(60)
+    batch.sync()
+    h.load(mixed, 60)
     batch.step(35)
     batch.sync()
     assert_same(h.snapshot(), exp, shape.island_size)

@@ -95,9 +95,18 @@ StepKernel pick_fitness(uint32_t surface_words, uint32_t tsize)
 }
 
 // Kernels without the closed-form curation path, for launches whose counters all equal the
-// generation: 16-byte trait records, tournament size 5 (the paper's, Sec. 3).
-StepKernel pick_uniform(uint32_t island_size)
+// generation: 16-byte records, tournament size 5 (the paper's, Sec. 3); trait model for every
+// island size, float-fitness model for islands of 16, 32 and 64.
+StepKernel pick_uniform(uint32_t island_size, uint32_t model)
 {
+    if (model == GA_MODEL_FITNESS) {
+        switch (island_size) {
+        case 16: return island_step_kernel<16, 2, 5, 1, 0>;
+        case 32: return island_step_kernel<32, 2, 5, 1, 0>;
+        case 64: return island_step_kernel<64, 2, 5, 1, 0>;
+        default: return nullptr;
+        }
+    }
     switch (island_size) {
     case 4: return island_step_kernel<4, 2, 5, 0, 0>;
     case 8: return island_step_kernel<8, 2, 5, 0, 0>;
@@ -213,12 +222,11 @@ cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t
                                uint32_t n_gens, bool migrate, cudaStream_t stream)
 {
     const bool uniform = run->cfg.mode == GA_SYNC && run->counters_uniform &&
-                         run->cfg.model == GA_MODEL_TRAIT && run->surface_words <= 2 &&
-                         run->cfg.tournament_size == 5;
-    const StepKernel k =
-        uniform ? pick_uniform(run->cfg.island_size)
-                : pick_kernel(run->cfg.island_size, run->surface_words, run->cfg.tournament_size,
-                              run->cfg.model);
+                         run->surface_words <= 2 && run->cfg.tournament_size == 5;
+    StepKernel k = uniform ? pick_uniform(run->cfg.island_size, run->cfg.model) : nullptr;
+    if (!k)
+        k = pick_kernel(run->cfg.island_size, run->surface_words, run->cfg.tournament_size,
+                        run->cfg.model);
     if (!k) return cudaErrorInvalidValue;
     StepArgs a;
     a.r = run_params(run, src, dst, g0, n_gens, migrate);

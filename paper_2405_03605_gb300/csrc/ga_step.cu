@@ -95,10 +95,27 @@ StepKernel pick_fitness(uint32_t surface_words, uint32_t tsize)
 }
 
 // Kernels without the closed-form curation path, for launches whose counters all equal the
-// generation: 16-byte records, tournament size 5 (the paper's, Sec. 3); trait model for every
-// island size, float-fitness model for islands of 16, 32 and 64.
-StepKernel pick_uniform(uint32_t island_size, uint32_t model)
+// generation, tournament size 5 (the paper's, Sec. 3): 16-byte trait records for every island
+// size, 32- and 48-byte trait records and the float-fitness model for islands of 16, 32 and 64.
+template <int N>
+StepKernel pick_uniform_wide(uint32_t surface_words)
 {
+    if (surface_words <= 6) return island_step_kernel<N, 6, 5, 0, 0>;
+    if (surface_words <= 8) return island_step_kernel<N, 8, 5, 0, 0>;
+    return nullptr;
+}
+
+StepKernel pick_uniform(uint32_t island_size, uint32_t surface_words, uint32_t model)
+{
+    if (surface_words > 2) {
+        if (model != GA_MODEL_TRAIT) return nullptr;
+        switch (island_size) {
+        case 16: return pick_uniform_wide<16>(surface_words);
+        case 32: return pick_uniform_wide<32>(surface_words);
+        case 64: return pick_uniform_wide<64>(surface_words);
+        default: return nullptr;
+        }
+    }
     if (model == GA_MODEL_FITNESS) {
         switch (island_size) {
         case 16: return island_step_kernel<16, 2, 5, 1, 0>;
@@ -222,8 +239,9 @@ cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t
                                uint32_t n_gens, bool migrate, cudaStream_t stream)
 {
     const bool uniform = run->cfg.mode == GA_SYNC && run->counters_uniform &&
-                         run->surface_words <= 2 && run->cfg.tournament_size == 5;
-    StepKernel k = uniform ? pick_uniform(run->cfg.island_size, run->cfg.model) : nullptr;
+                         run->cfg.tournament_size == 5;
+    StepKernel k =
+        uniform ? pick_uniform(run->cfg.island_size, run->surface_words, run->cfg.model) : nullptr;
     if (!k)
         k = pick_kernel(run->cfg.island_size, run->surface_words, run->cfg.tournament_size,
                         run->cfg.model);

@@ -191,7 +191,10 @@ int ga_snapshot_device(ga_run *run, void *device_dst, size_t cap, size_t *writte
 
 /* Replace the population with canonical records from host_src and set the generation
    counter (checkpoint resume; bit-exact because draws are keyed by generation).  bytes
-   must equal n_agents * record_bytes.  Synchronous. */
+   must equal n_agents * record_bytes.  Agents may carry any counters; in GA_SYNC mode a
+   device pass checks whether every counter equals `generation` (the usual case, a snapshot of
+   a synchronous run), and later steps use kernels without the closed-form curation path only
+   then.  Synchronous. */
 int ga_load(ga_run *run, const void *host_src, size_t bytes, uint64_t generation);
 
 /*

@@ -121,23 +121,49 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
     for (int ag = 0; ag < A; ++ag) {
         uint32_t best = 0;
         int best_trait = 0;
+        if constexpr (TS > 0) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if constexpr (TS > 0) {
-                if (i >= TS) break;
-            } else {
-                if (static_cast<uint32_t>(i) >= p.tsize) break;
+            for (int i = 0; i < TS; ++i) {
+                const uint32_t word = i < 4 ? w[ag].x : w[ag].y;
+                uint32_t sel = word >> (8 * (i & 3) + 8 - LOGN);
+                if constexpr (N > 32) sel &= N - 1u;
+                const int t = candidate_trait<N, A, SEG>(mask, trait, sel);
+                bool better;
+                if constexpr (MODEL == 1) better = __int_as_float(t) > __int_as_float(best_trait);
+                else better = t > best_trait;
+                if (i == 0 || better) {
+                    best = sel;
+                    best_trait = t;
+                }
             }
-            const uint32_t word = i < 4 ? w[ag].x : w[ag].y;
-            uint32_t sel = word >> (8 * (i & 3) + 8 - LOGN);
-            if constexpr (N > 32) sel &= N - 1u;
-            const int t = candidate_trait<N, A, SEG>(mask, trait, sel);
-            bool better;
-            if constexpr (MODEL == 1) better = __int_as_float(t) > __int_as_float(best_trait);
-            else better = t > best_trait;
-            if (i == 0 || better) {
-                best = sel;
-                best_trait = t;
+        } else {
+            // size n from the run (1..8): draws n-1 down to 0, each replacing the best when at
+            // least as good, from a start below every trait (INT_MIN; -inf for the float model,
+            // whose fitness is never NaN) -- the earliest maximal draw is kept, as above, and the
+            // switch enters the unrolled draws once instead of testing n at every draw
+            best_trait = MODEL == 1 ? static_cast<int>(0xFF800000u) : static_cast<int>(0x80000000u);
+            auto draw = [&](const int i) {
+                const uint32_t word = i < 4 ? w[ag].x : w[ag].y;
+                uint32_t sel = word >> (8 * (i & 3) + 8 - LOGN);
+                if constexpr (N > 32) sel &= N - 1u;
+                const int t = candidate_trait<N, A, SEG>(mask, trait, sel);
+                bool better;
+                if constexpr (MODEL == 1) better = __int_as_float(t) >= __int_as_float(best_trait);
+                else better = t >= best_trait;
+                if (better) {
+                    best = sel;
+                    best_trait = t;
+                }
+            };
+            switch (p.tsize) {
+            case 8: draw(7); [[fallthrough]];
+            case 7: draw(6); [[fallthrough]];
+            case 6: draw(5); [[fallthrough]];
+            case 5: draw(4); [[fallthrough]];
+            case 4: draw(3); [[fallthrough]];
+            case 3: draw(2); [[fallthrough]];
+            case 2: draw(1); [[fallthrough]];
+            default: draw(0);
             }
         }
         win[ag] = best;

@@ -650,28 +650,38 @@ static void async_clear(orc_state *st)
 }
 
 /*
- * Migration step of island `isl` at its generation g (Sec. 2: the loop copies in the genomes
- * whose receive completed, then refills the send buffers whose send completed, with randomly
- * sampled members).  Reading used here: each island has one send buffer per direction
- * holding at most one genome; a send completes when the neighbour takes the genome out.
- *   1. collect: for d = N, S, E, W in order, the partial Fisher-Yates draw of the synchronous
- *      mode swaps position d with r_d (whether or not anything arrives); if the buffer of
- *      neighbour nb(d) facing isl (nb(d)'s direction opposite to d) is full, its genome is
- *      taken out (the buffer becomes empty) and replaces the member in position d;
- *   2. refill: for each d whose own buffer towards d is empty, a copy of member e_d = (bits
- *      8..15 of word 3 of slot d's draw) * N >> 8 of the island as it stands after step 1
- *      fills it -- unless that member's counter is 2^32 - 1 (such a genome is never sent).
+ * Migration step of island `isl` at its generation g (Sec. 2: the update loop first tests
+ * every completion flag; then, for each receive that completed, the arrived genome replaces
+ * a randomly chosen member; then, for each send that completed, the send buffer is refilled
+ * with a randomly sampled member; only after that are flags reset and new sends started).
+ * Reading used here: each island has one send buffer per direction holding at most one
+ * genome; a send completes when the neighbour takes the genome out.
+ *   1. test: R_d = the buffer of neighbour nb(d) facing isl (nb(d)'s direction opposite to
+ *      d) is full; E_d = isl's own buffer towards d is empty -- all eight tested first;
+ *   2. collect: for d = N, S, E, W in order, the partial Fisher-Yates draw of the synchronous
+ *      mode swaps position d with r_d (whether or not anything arrives); if R_d, the genome
+ *      is taken out of the buffer (which becomes empty) and replaces the member in position d;
+ *   3. refill: for each d with E_d, a copy of member e_d = (bits 8..15 of word 3 of slot d's
+ *      draw) * N >> 8 of the island as it stands after step 2 fills isl's buffer towards d.
+ * The flags are only ever changed by the island that owns a buffer (fill) and by the one
+ * that takes from it, so testing them first differs from testing each one when it is used
+ * only where an island is its own neighbour (one-row or one-column tori): a buffer that the
+ * island empties itself in step 2 was full when tested and is refilled a pass later.
  * arrivals (optional, 4 per island) counts deliveries per direction.
  */
 static void async_migrate_island(orc_state *st, uint32_t isl, uint32_t g, uint64_t *arrivals)
 {
     const orc_config *c = &st->cfg;
     const uint32_t N = c->island_size, words = st->words;
-    uint32_t w3[4];
+    uint32_t w3[4], in_box[4];
+    int full_in[4], empty_out[4];
     for (uint32_t d = 0; d < 4; ++d) {
         uint32_t w[4];
         draw(c->seed, g, isl, d, ORC_PURPOSE_BIRTH, c->run_id, w);
         w3[d] = w[3];
+        in_box[d] = neighbour(c, isl, (int)d) * 4 + (d ^ 1u);
+        full_in[d] = st->mail_full[in_box[d]] != 0;
+        empty_out[d] = st->mail_full[isl * 4 + d] == 0;
     }
     uint32_t perm[256];
     for (uint32_t j = 0; j < N; ++j) perm[j] = j;
@@ -680,9 +690,8 @@ static void async_migrate_island(orc_state *st, uint32_t isl, uint32_t g, uint64
         uint32_t tmp = perm[d];
         perm[d] = perm[r];
         perm[r] = tmp;
-        const uint32_t box = neighbour(c, isl, (int)d) * 4 + (d ^ 1u);
-        if (!st->mail_full[box]) continue;
-        const uint32_t dst = isl * N + perm[d];
+        if (!full_in[d]) continue;
+        const uint32_t box = in_box[d], dst = isl * N + perm[d];
         st->trait[dst] = st->mail_trait[box];
         st->counter[dst] = st->mail_counter[box];
         memcpy(&st->surface[(size_t)dst * words], &st->mail_surface[(size_t)box * words],
@@ -692,9 +701,9 @@ static void async_migrate_island(orc_state *st, uint32_t isl, uint32_t g, uint64
         if (arrivals) arrivals[isl * 4 + d] += 1;
     }
     for (uint32_t d = 0; d < 4; ++d) {
+        if (!empty_out[d]) continue;
         const uint32_t e = (((w3[d] >> 8) & 0xFFu) * N) >> 8;
         const uint32_t src = isl * N + e, box = isl * 4 + d;
-        if (st->mail_full[box] || st->counter[src] == 0xFFFFFFFFu) continue;
         st->mail_trait[box] = st->trait[src];
         st->mail_counter[box] = st->counter[src];
         memcpy(&st->mail_surface[(size_t)box * words], &st->surface[(size_t)src * words],

@@ -4,10 +4,11 @@ waiting) on its sequential schedule, and for the lineage tracking the pins rely 
 What fixes the asynchronous mode independently of its own code:
   - with migration off it must be the synchronous GA exactly (the reproduction path);
   - the number of deliveries per (island, direction) follows from the protocol alone (a send
-    buffer holds one genome and is refilled only once its genome was taken; an island
-    takes before it refills): within each window an earlier neighbour delivers once, a
-    later one delivers what it sent in the previous window, and an island that is its own
-    neighbour delivers in every generation but its first;
+    buffer holds one genome and is refilled only once its genome was taken; every flag is
+    tested before anything moves, as the Sec. 2 loop does): within each window an earlier
+    neighbour delivers once, a later one delivers what it sent in the previous window, and
+    an island that is its own neighbour delivers every second generation (the buffer it
+    empties itself tested full, so it is refilled one pass later);
   - on populations it produces, whose counters drift apart, the mixed-counter MRCA bounds
     must bracket the true divergence rank known from the recorded pedigree.
 """
@@ -53,7 +54,7 @@ def test_arrival_counts(rows, cols, window):
     for isl in range(rows * cols):
         for d in range(4):
             nb = _neighbour(rows, cols, isl, d)
-            want = k if nb < isl else k - 1 if nb > isl else k * window - 1
+            want = k if nb < isl else k - 1 if nb > isl else (k * window) // 2
             assert arr[isl, d] == want, (isl, d, nb, arr[isl, d], want)
 
 
@@ -150,11 +151,10 @@ def test_async_mrca_lower_bound_rate(policy, S, b):
     assert misses / trials <= p_miss + 4 * np.sqrt(p_miss / trials)
 
 
-def test_counter_limit_is_never_sent():
-    """A genome whose counter is 2^32 - 1 stays home (that record value marks an empty
-    buffer).  On a 1 x 3 ring whose members all carry it at generation 0, nothing is sent in
-    generation 0, so in generation 1 island 0 (which runs first) finds nothing from islands
-    1 and 2; from an ordinary population it finds a genome from each."""
+def test_every_counter_value_is_sent():
+    """The protocol has no reserved genome value: a member is sent whatever its counter (here
+    2^32 - 1 and 7).  On a 1 x 3 ring, every buffer filled in generation 0 is taken in
+    generation 1 by island 0 (which runs first) from its east and west neighbours."""
     def first_island_arrivals(counter):
         run = OracleRun(1, 3, island_size=16, seed=8)
         rec = run.snapshot()
@@ -162,8 +162,18 @@ def test_counter_limit_is_never_sent():
         run.load(rec, 0)
         run.step_async(1, window=1)
         return run.step_async(1, window=1)[0]
-    assert first_island_arrivals(0xFFFFFFFF).sum() == 0
-    assert first_island_arrivals(7)[2:].tolist() == [1, 1]  # east and west neighbours
+    assert first_island_arrivals(0xFFFFFFFF)[2:].tolist() == [1, 1]
+    assert first_island_arrivals(7)[2:].tolist() == [1, 1]
+
+
+def test_own_buffer_tested_before_taking():
+    """Sec. 2 order on a 1 x 1 torus (every neighbour is the island itself): generation 0
+    tests all four own buffers empty and fills them; generation 1 tests them full, takes all
+    four back and leaves them empty (they were full when tested); generation 2 takes nothing
+    and refills them."""
+    run = OracleRun(1, 1, island_size=16, seed=4)
+    per_gen = [run.step_async(1, window=1)[0].tolist() for _ in range(4)]
+    assert per_gen == [[0, 0, 0, 0], [1, 1, 1, 1], [0, 0, 0, 0], [1, 1, 1, 1]]
 
 
 def test_load_clears_mailboxes():

@@ -137,14 +137,17 @@ int ga_migrate_policy(ga_run *run, uint32_t per_neighbor, uint32_t every_k);
  * sends and receives and never waits for them).  Each island owns one send buffer per
  * direction, holding at most one genome; a send completes when the neighbour takes the
  * genome out.  On each of its migration generations g (g mod every_k == 0) an island, in
- * this order: (1) for directions N, S, E, W takes the genome out of each full buffer facing
- * it (the buffer becomes empty) and lands it in the slot chosen by the partial Fisher-Yates
- * draw of GA_SYNC (missing arrivals leave their slot alone); (2) fills each of its own
- * buffers that is empty with a copy of member e_d = (bits 8..15 of word 3 of its slot-d
- * birth draw) * N >> 8, unless that member's counter is 2^32 - 1 (never sent: that record
- * value marks an empty buffer); then (3) reproduces as in GA_SYNC.  Nothing ever waits.
- * A migrant keeps its counter, so counters drift apart and each deposit uses the site of
- * the agent's own counter.
+ * this order: (0) tests every buffer facing it and each of its own buffers; (1) for
+ * directions N, S, E, W takes the genome out of each buffer facing it that tested full (the
+ * buffer becomes empty) and lands it in the slot chosen by the partial Fisher-Yates draw of
+ * GA_SYNC (missing arrivals leave their slot alone); (2) fills each of its own buffers that
+ * tested empty with a copy of member e_d = (bits 8..15 of word 3 of its slot-d birth draw)
+ * * N >> 8; then (3) reproduces as in GA_SYNC.  Nothing ever waits.  Only where an island
+ * is its own neighbour (one-row or one-column tori) can a buffer change between (0) and (2):
+ * one it empties itself in (1) is refilled a pass later.  A migrant keeps its counter, so
+ * counters drift apart and each deposit uses the site of the agent's own counter.  Counter
+ * 2^32 - 1 is reserved (it marks an empty buffer): a birth that produces it makes the run
+ * invalid, reported as GA_ESTATE by the next ga_sync or ga_snapshot.
  *
  * A launch runs `window` generations of every island (all islands start it at the same
  * generation).  With window 1 no island gets more than a generation ahead of another, as
@@ -191,7 +194,8 @@ int ga_snapshot_device(ga_run *run, void *device_dst, size_t cap, size_t *writte
 
 /* Replace the population with canonical records from host_src and set the generation
    counter (checkpoint resume; bit-exact because draws are keyed by generation).  bytes
-   must equal n_agents * record_bytes.  Agents may carry any counters; in GA_SYNC mode a
+   must equal n_agents * record_bytes.  Agents may carry any counters, except 2^32 - 1 in the
+   asynchronous modes (reserved: it marks an empty send buffer; GA_EINVAL); in GA_SYNC mode a
    device pass checks whether every counter equals `generation` (the usual case, a snapshot of
    a synchronous run), and later steps use kernels without the closed-form curation path only
    then.  Synchronous. */
@@ -211,9 +215,10 @@ int ga_load(ga_run *run, const void *host_src, size_t bytes, uint64_t generation
  * In the asynchronous modes agents i and j may hold different counters Ti and Tj: the
  * ranks compared are those retained by both (a rank sits at the same site in both tables,
  * so these are the sites whose rank tables at Ti and Tj agree), in ascending order, and the
- * same rule applies to that list with hi = min(Ti, Tj) when nothing mismatches.  Cost
- * O(Tmin + n (Tmax - Tmin)) curation evaluations for the rank tables (Tmin, Tmax: the
- * smallest and largest sampled counter) plus O(n^2 S) for the pairs.
+ * same rule applies to that list with hi = min(Ti, Tj) when nothing mismatches.  The
+ * retained ranks at a counter come from the curation rule in closed form, without replaying
+ * earlier ranks: O(S) work per distinct table, O(n^2) (GA_SYNC) or O(n^2 S) (mixed
+ * counters) for the pairs.
  * Synchronous.  Scratch memory is allocated and freed on the run's stream.
  * Errors: GA_EINVAL (n < 2, n > 65536, id out of range, null pointers), GA_ESTATE
  * (GA_SYNC mode and counters differ), GA_ENOMEM, GA_ECUDA.
@@ -312,21 +317,42 @@ int ga_curation_sites(uint32_t policy, uint32_t surface_sites, uint32_t t0, uint
  *   generation     T, the counter every sampled agent must hold;
  *   d_agent_ids    n device uint32 ids, 2 <= n <= 4096 (larger n: GA_EINVAL);
  *   d_lo, d_hi     n(n-1)/2 device uint32 each, pairs in row-major upper-triangle order.
- * Its scratch (about 135 KB) is a fixed array inside the library's device image, which
- * every GPU that loads the library holds until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress, with the device
- * current); make that first call before any stream capture.  All calls on a device share
- * the one array and each call overwrites it, so calls that overlap on the GPU (from several
- * host threads or streams at once) race and must be serialised by the caller.
- * Synchronous: enqueues on `stream` (NULL: default stream), waits for it, and returns
- * GA_ESTATE when an agent's counter differs from T, GA_EINVAL for an id >= n_agents,
- * GA_EINVAL for invalid arguments, GA_ECUDA for runtime failures.  It calls no cudaMalloc,
- * cudaFree or other allocating routine.
+ * Its scratch (133,632 bytes) is a fixed array inside the library's device image, which
+ * every GPU that loads the library holds until the process exits.  Each call looks up that
+ * array's device address (cudaGetSymbolAddress, with the caller's device current), so it
+ * stays valid after a device reset.  All calls on a device share the one array and each call
+ * overwrites it, so calls that overlap on the GPU (from several host threads or streams at
+ * once) race and must be serialised by the caller.
+ * Synchronous: enqueues on `stream` (NULL: default stream) and waits for it, so it must not
+ * be called while that stream is being captured into a CUDA graph.  Returns GA_ESTATE when
+ * an agent's counter differs from T, GA_EINVAL for an id >= n_agents, GA_EINVAL for invalid
+ * arguments, GA_ECUDA for runtime failures (an error left pending by earlier work on the
+ * calling thread is cleared first and not reported).  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
  */
 int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_bytes, uint32_t n_agents,
                            uint32_t curation, uint32_t surface_sites, uint32_t differentia_bits,
                            uint32_t generation, const uint32_t *d_agent_ids, uint32_t n,
                            uint32_t *d_lo, uint32_t *d_hi, void *stream);
+
+/*
+ * Integer-pipe throughput probe.  The paper has no counterpart: a measurement aid that gives
+ * a measured ceiling for the island step's integer work, next to the nominal issue limit.
+ * Runs, on the current device, 8 resident blocks of 256 threads per SM, each thread
+ * independent chains of one operation `kind` (eight chains of 32 steps per iteration; for
+ * GA_PEAK_MIX two Philox states of 16 rounds), `iters` iterations, after a short warm-up;
+ * times the launch with CUDA events on `stream` (NULL: default stream).
+ *   GA_PEAK_LOP3  three-input logic (lop3.b32)
+ *   GA_PEAK_IMAD  32 x 32 -> 64-bit multiply-add (mad.wide.u32)
+ *   GA_PEAK_MIX   Philox4x32 rounds: two 32 x 32 -> 64-bit multiplies and two three-input
+ *                 XORs each (the island step's random-number arithmetic)
+ * *ops_per_s gets operations (one per PTX instruction above) per second; *seconds (optional)
+ * the timed launch's duration.  Synchronous.  Errors: GA_EINVAL, GA_ENOMEM, GA_ECUDA.
+ */
+#define GA_PEAK_LOP3 0u
+#define GA_PEAK_IMAD 1u
+#define GA_PEAK_MIX 2u
+int ga_int_peak(uint32_t kind, uint32_t iters, void *stream, double *ops_per_s, double *seconds);
 
 /* Destroy the run (synchronises its stream; frees library-owned memory).  A member of a
    batch is first removed from it, as by ga_batch_remove. */

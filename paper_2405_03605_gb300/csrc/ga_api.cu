@@ -229,6 +229,7 @@ int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_
     run->d_status = reinterpret_cast<int *>(base);
     run->d_flag = reinterpret_cast<int *>(base + ga::kStatusBytes / 2);
     run->d_sites = reinterpret_cast<int32_t *>(base + ga::kStatusBytes);
+    run->d_masks = reinterpret_cast<uint2 *>(base + ga::kMaskOffset);
     run->sites_base = 0;
     run->pop[0] = base + ga::kHeaderBytes;
     run->pop[1] = base + ga::kHeaderBytes + buffer_stride(cfg);
@@ -339,6 +340,15 @@ int ga_load(ga_run *run, const void *host_src, size_t bytes, uint64_t generation
 {
     if (!run || !host_src) return GA_EINVAL;
     if (bytes != population_bytes(&run->cfg) || generation > 0xFFFFFFFFull) return GA_EINVAL;
+    if (run->cfg.mode != GA_SYNC) {
+        // counter 2^32 - 1 is reserved in the asynchronous modes (it marks an empty buffer)
+        const uint8_t *rec = static_cast<const uint8_t *>(host_src);
+        for (uint32_t a = 0; a < run->n_agents; ++a) {
+            uint32_t c;
+            std::memcpy(&c, rec + static_cast<size_t>(a) * run->record_bytes + 4, sizeof c);
+            if (c == 0xFFFFFFFFu) return GA_EINVAL;
+        }
+    }
     if (cudaMemcpyAsync(run->pop[run->cur], host_src, bytes, cudaMemcpyHostToDevice,
                         run->stream) != cudaSuccess)
         return GA_ECUDA;

@@ -8,8 +8,14 @@
 // waits: a buffer that is not ready is simply skipped, so islands exchange migrants at
 // whatever pace the hardware runs them, and a migrant keeps the counter of its lineage
 // (deposits then follow each agent's own counter, as in the synchronous kernels'
-// closed-form branch).  A genome whose counter is 2^32 - 1 is never sent (that record value
-// marks an empty buffer).
+// closed-form branch).  The loop tests every flag before anything moves (Sec. 2), so a buffer
+// that an island empties itself -- only possible where it is its own neighbour, on one-row
+// or one-column tori -- tested full and is refilled a pass later.
+//
+// Counter 2^32 - 1 is reserved: the 16-byte buffers mark "empty" with an all-ones record.
+// ga_load refuses such counters in the asynchronous modes, and a birth that would produce
+// one records GA_ESTATE in the run's status word (the run is then invalid; such a genome is
+// never put into a buffer).
 //
 // Two handoff protocols, both single producer / single consumer and wait-free:
 //
@@ -33,9 +39,10 @@
 //
 // On tori with one row or one column an island is its own neighbour, so its own lanes sit
 // on both sides of a buffer: there the takes are made at the start of the generation and the
-// refills after them, between warp barriers, and publication is immediate.  On the
-// sequential schedule (one island per launch) every variant gives the same result as the
-// oracle's model: take, land, then refill what is empty.
+// refills after them, between warp barriers, publication is immediate, and a buffer the
+// island has just taken a genome out of is left empty for this pass.  On the sequential
+// schedule (one island per launch) every variant gives the same result as the oracle's
+// model: test, take and land, then refill what tested empty.
 //
 // Draws: the birth draws of the synchronous mode, keyed by the generation the island is
 // running.  For direction d, word 3 of slot d's draw supplies bits 16..31 for the landing
@@ -62,6 +69,16 @@ RunParams run_params(const ga_run *run, const void *src, void *dst, uint32_t g0,
 namespace {
 
 constexpr uint32_t kNeverSent = 0xFFFFFFFFu;  // counter value of the empty-buffer record
+
+// A birth gave a counter of 2^32 - 1, the value reserved for empty buffers: the run is
+// invalid from here on (GA_ESTATE, returned by the next ga_sync / ga_snapshot).
+template <int A, int LW>
+__device__ __forceinline__ void check_counters(const uint32_t (&rec)[A][LW], int *status)
+{
+#pragma unroll
+    for (int ag = 0; ag < A; ++ag)
+        if (rec[ag][1] == kNeverSent) atomicCAS(status, 0, -5);
+}
 
 // GPU-scope memory-model accesses to the send buffers (global memory, 16-byte aligned).
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
@@ -188,6 +205,7 @@ island_async_kernel(const AsyncArgs a)
     const bool taker = seg_lane < 4u;
     const bool sender = seg_lane >= 4u && seg_lane < 8u;
     uint4 *box = nullptr;
+    bool self_nb = false;  // taker lane: the neighbour in direction d is this island
     if (taker) {
         const uint32_t y = div_cols(island, p.cols_m, p.cols_l), x = island - y * p.cols;
         const uint32_t yn = d == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
@@ -195,6 +213,7 @@ island_async_kernel(const AsyncArgs a)
         const uint32_t xn = d == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
                           : d == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
         const uint32_t nb = yn * p.cols + xn;
+        self_nb = nb == island;
         box = a.mail + (static_cast<size_t>(in_bounds(nb < p.n_islands, p.status) ? nb : island) * 4u +
                         (d ^ 1u)) * MB;
     } else if (sender) {
@@ -318,7 +337,12 @@ island_async_kernel(const AsyncArgs a)
                     out[k] = val;
                 }
             }
-            const bool sendable = sender && out[1] != kNeverSent;
+            // a buffer this island took a genome out of itself in this pass (its own
+            // buffer towards d ^ 1, taken by its lane d) tested full: no refill now
+            const uint32_t self_took =
+                early ? 0u : (__ballot_sync(mask, arrived && self_nb) >> (lane - seg_lane)) & 0xFu;
+            const bool sendable =
+                sender && out[1] != kNeverSent && ((self_took >> (d ^ 1u)) & 1u) == 0u;
             if (!early) __syncwarp(mask);  // after this generation's takes by this warp
             if constexpr (kAtomic) {
                 if (sendable) refill128(box, out);
@@ -349,6 +373,7 @@ island_async_kernel(const AsyncArgs a)
         // 3. evaluation, selection, mutation, deposit
         reproduce<N, SW, TS, MODEL>(rec, w, p, a.rk, island, seg_lane, mask, g,
                                     gen_site_at(p, it));
+        check_counters(rec, p.status);
     }
     if constexpr (!kAtomic) {
         if (pending) st_release(flag, 1u);
@@ -376,7 +401,7 @@ island_async_kernel(const AsyncArgs a)
 // land the arrivals, refill their own buffers (lanes 4..7, compare-and-swap) from the island
 // as it now stands, and reproduce.  Every take of the launch precedes every refill (block
 // barrier), so an island that is its own neighbour takes what it sent in the previous
-// generation, as in the one-warp kernel.
+// generation and leaves that buffer empty for this pass, as in the one-warp kernel.
 template <int N, int TS, int MODEL>
 __global__ void __launch_bounds__(kAsyncThreads) island_async_gen_kernel(const AsyncArgs a)
 {
@@ -387,6 +412,7 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_gen_kernel(const A
     constexpr uint32_t kNone = 0xFFFFFFFFu;  // no arrival from that direction
     __shared__ uint4 s_got[ML];
     __shared__ __align__(16) uint32_t s_slot[ML];
+    __shared__ uint8_t s_self[ML];  // by (island, direction): own buffer emptied by itself
     const RunParams &p = a.r;
     const uint32_t g = p.g0;
 
@@ -406,6 +432,7 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_gen_kernel(const A
     const uint32_t md = threadIdx.x & 3u;
     uint32_t r = md;
     uint4 got = make_uint4(~0u, ~0u, ~0u, ~0u);
+    bool self_nb = false;
     if (bk) {
         const uint32_t isl = island0 + (threadIdx.x >> 2);
         if (isl < a.last) {
@@ -417,6 +444,7 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_gen_kernel(const A
             const uint32_t xn = md == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
                               : md == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
             const uint32_t nb = yn * p.cols + xn;
+            self_nb = nb == isl;
             if (in_bounds(nb < p.n_islands, p.status))
                 got = take128(a.mail + (static_cast<size_t>(nb) * 4u + (md ^ 1u)));
         }
@@ -458,6 +486,8 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_gen_kernel(const A
             }
             s_got[threadIdx.x] = got;
             s_slot[threadIdx.x] = got.y != kNeverSent ? slot : kNone;
+            // this lane took from the island's own buffer towards md ^ 1 (entry t ^ 1)
+            s_self[threadIdx.x ^ 1u] = self_nb && got.y != kNeverSent;
         }
         __syncthreads();
     }
@@ -497,10 +527,11 @@ __global__ void __launch_bounds__(kAsyncThreads) island_async_gen_kernel(const A
                 out[k] = val;
             }
         }
-        if (seg_lane >= 4u && seg_lane < 8u && out[1] != kNeverSent)
+        if (seg_lane >= 4u && seg_lane < 8u && out[1] != kNeverSent && !s_self[4 * local + d])
             refill128(a.mail + (static_cast<size_t>(island) * 4u + d), out);
     }
     reproduce<N, 2, TS, MODEL>(rec, w, p, a.rk, island, seg_lane, mask, g, gen_site_at(p, 0u));
+    check_counters(rec, p.status);
 #pragma unroll
     for (int ag = 0; ag < A; ++ag)
         p.dst[static_cast<size_t>(island) * N + seg_lane + 32u * ag] =

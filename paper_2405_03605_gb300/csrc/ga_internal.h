@@ -35,6 +35,7 @@ struct ga_run {
     ga_batch *batch;     // the batch this run belongs to, if any
     bool counters_uniform;  // every agent's counter equals `generation` (founder, sync steps)
     int *d_flag;         // device scratch word for ga_load's counter check (workspace header)
+    uint2 *d_masks;      // deposit masks of generation sites_base + i (workspace header)
 };
 
 namespace ga {
@@ -59,10 +60,12 @@ cudaError_t launch_dependent(void (*kernel)(P...), dim3 grid, dim3 block, cudaSt
 }
 
 // Workspace header: the device status word (first 256 bytes), then the curation-site table
-// of the generations a ga_step call is about to run (one int32 per generation).
+// of the generations a ga_step call is about to run (one int32 per generation), then their
+// deposit masks (two uint32 per generation; filled for surfaces of at most 64 bits).
 constexpr size_t kStatusBytes = 256;
 constexpr uint32_t kSiteTableCap = 4096;
-constexpr size_t kHeaderBytes = kStatusBytes + kSiteTableCap * sizeof(int32_t);
+constexpr size_t kMaskOffset = kStatusBytes + kSiteTableCap * sizeof(int32_t);
+constexpr size_t kHeaderBytes = kMaskOffset + kSiteTableCap * 2 * sizeof(uint32_t);
 
 // Largest number of generations one island-step launch runs without migration.
 constexpr uint32_t kMaxGensPerLaunch = 256;
@@ -95,7 +98,10 @@ cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_
                                 cudaStream_t stream);
 int async_step(ga_run *run, uint32_t n_gens, cudaStream_t stream);
 
+// Curation sites of ranks [t0, t0 + count); with d_masks (S * bits <= 64) also the deposit
+// masks of those ranks.
 cudaError_t launch_curation_sites(uint32_t policy, uint32_t sites, uint32_t t0, uint32_t count,
-                                  int32_t *d_sites, cudaStream_t stream);
+                                  int32_t *d_sites, cudaStream_t stream, uint32_t bits = 0,
+                                  uint2 *d_masks = nullptr);
 
 }  // namespace ga

@@ -42,6 +42,11 @@ struct RunParams {
     float effect_scale;                     // fitness model: mutation amount scale
     uint32_t gen_sites_left;                // entries of gen_sites from g0 on
     int *status;                            // the run's device status word
+    // deposit masks of generation g0 + i (records with a 64-bit surface, S b <= 64): the bits of
+    // surface words 0 and 1 that the generation's deposit overwrites, (0, 0) for none; the
+    // differentia (low b bits of the draw) is spread over every b-bit field by one multiply
+    const uint2 *__restrict__ gen_masks;
+    uint32_t dif_mask, dif_rep;             // 2^b - 1 and the b-bit repetition pattern
 };
 
 // Curation site of generation g0 + it from the launch's site table (-1, no deposit, if a
@@ -49,6 +54,13 @@ struct RunParams {
 __device__ __forceinline__ int gen_site_at(const RunParams &p, uint32_t it)
 {
     return in_bounds(it < p.gen_sites_left, p.status) ? __ldg(&p.gen_sites[it]) : -1;
+}
+
+// Deposit masks of generation g0 + it ((0, 0), no deposit, if a device-check build finds `it`
+// past the table).
+__device__ __forceinline__ uint2 gen_mask_at(const RunParams &p, uint32_t it)
+{
+    return in_bounds(it < p.gen_sites_left, p.status) ? __ldg(&p.gen_masks[it]) : make_uint2(0u, 0u);
 }
 
 // Candidate trait of slot `sel` of this lane's island.  For N <= 32 `sel` may carry extra
@@ -103,11 +115,15 @@ static __device__ __noinline__ int curation_site_of(uint32_t policy, uint32_t lo
 // launches in which every counter equals the generation (synchronous runs whose counters
 // were never loaded mixed), where it would never be taken.
 // MODEL 0: int32 trait, +1 / -1; MODEL 1: float fitness, -/+ effect_scale * |normal|.
-template <int N, int SW, int TS, int MODEL, int CF = 1>
+// DM = 1 (64-bit surfaces, every counter equal to g): the deposit takes the generation's
+// precomputed masks `dmask` instead of the site: the differentia spread over every b-bit
+// field, kept where the mask is set -- the same bits as writing it at site * b.
+template <int N, int SW, int TS, int MODEL, int CF = 1, int DM = 0>
 __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
                                           const uint4 (&w)[Shape<N>::A], const RunParams &p,
                                           const RoundKeys &rk, uint32_t island, uint32_t seg_lane,
-                                          unsigned mask, uint32_t g, int gen_site)
+                                          unsigned mask, uint32_t g, int gen_site,
+                                          uint2 dmask = make_uint2(0u, 0u))
 {
     constexpr int A = Shape<N>::A, SEG = Shape<N>::SEG, LOGN = Shape<N>::LOGN;
     constexpr int LW = 2 + SW;
@@ -215,8 +231,14 @@ __device__ __forceinline__ void reproduce(uint32_t (&rec)[Shape<N>::A][2 + SW],
         if constexpr (CF != 0) {
             if (c != g) site = curation_site_of(p.policy, p.log2_sites, p.sites, c);
         }
-        if (site >= 0 && in_bounds(static_cast<uint32_t>(site) < p.sites && site * p.bits < 32u * SW,
-                                   p.status)) {
+        if constexpr (DM != 0) {
+            static_assert(SW == 2 && CF == 0, "mask deposits: 64-bit surfaces, uniform counters");
+            const uint32_t rep = (w[ag].w & p.dif_mask) * p.dif_rep;
+            child[ag][2] = (child[ag][2] & ~dmask.x) | (rep & dmask.x);
+            child[ag][3] = (child[ag][3] & ~dmask.y) | (rep & dmask.y);
+        } else if (site >= 0 && in_bounds(static_cast<uint32_t>(site) < p.sites &&
+                                              site * p.bits < 32u * SW,
+                                          p.status)) {
             const uint32_t pos = static_cast<uint32_t>(site) * p.bits;
             const uint32_t wi = pos >> 5, sh = pos & 31u;
             const uint32_t m = ((1u << p.bits) - 1u) << sh;
@@ -410,6 +432,125 @@ __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &
             for (int e = 0; e < 4; ++e) w4[e] = (4 * q + e < LW) ? rec[ag][4 * q + e] : 0u;
             p.dst[agent * Q + q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Multi-unit blocks for 32-agent islands with 16-byte records whose counters all equal the
+// generation (the paper-scale workload).  A block of 8 warps runs U units of 8 islands in
+// turn; warp w runs island w of every unit.  Each island's records come into shared memory by
+// asynchronous copies (cp.async): the next unit's while the current one is computed, so a
+// warp never waits for a record load except the block's first.  The migration bookkeeping of
+// all U units is done once, at the start, by warps 0..U-1 (warp u: unit u, one lane per
+// (island, direction), as in step_block), so it is spread over the block's warps instead of
+// all falling to warp 0, and its immigrant copies go straight into shared memory.  An
+// island's lanes then find their landing direction in a per-island table of 32 bytes (0xFF:
+// no immigrant) and take the immigrant record from shared memory.  Deposits use the
+// generation's precomputed masks.  The only block barrier is the one after the bookkeeping.
+// ---------------------------------------------------------------------------------------
+
+// 16-byte asynchronous global -> shared copy (bypassing L1), and its group operations.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" :: "r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" :: "n"(PENDING) : "memory"); }
+
+template <int TS, int U>
+__device__ __forceinline__ void step_units(const RunParams &p, const RoundKeys &rk, uint32_t blk)
+{
+    constexpr int N = 32, SW = 2, LW = 4, WARPS = 8;
+    static_assert(U >= 1 && U <= WARPS, "warp u does the bookkeeping of unit u");
+    __shared__ uint4 s_rec[WARPS][2][32];        // per warp: current and next island's records
+    __shared__ uint4 s_imm[U][WARPS * 4];        // immigrants by (unit, island, direction)
+    __shared__ __align__(16) uint8_t s_dir[U][WARPS][32];  // landing direction of each slot
+
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t island0 = blk * (U * WARPS);  // first island of the block's first unit
+
+    // the first unit's records
+    {
+        const uint32_t island = island0 + warp;
+        if (island < p.n_islands) cp_async16(&s_rec[warp][0][lane], &p.src[static_cast<size_t>(island) * N + lane]);
+        cp_async_commit();
+    }
+
+    // migration bookkeeping of unit `warp`: lane (island i, direction d); the birth draw of
+    // slot d carries the immigrant index (bits 8..15) and the landing draw (bits 16..31)
+    if (p.migrate && warp < static_cast<uint32_t>(U)) {
+        uint32_t *dirw = reinterpret_cast<uint32_t *>(&s_dir[warp][0][0]);
+        dirw[lane] = 0xFFFFFFFFu;
+        dirw[lane + 32u] = 0xFFFFFFFFu;
+        const uint32_t li = lane >> 2, md = lane & 3u;
+        const uint32_t isl = island0 + warp * WARPS + li;
+        const bool ok = isl < p.n_islands;
+        uint32_t r = md;
+        if (ok) {
+            const uint32_t u = philox_rk(p.g0, isl, md | (kBirth << 16), p.run_id, rk).w;
+            r = md + (((u >> 16) * static_cast<uint32_t>(N - md)) >> 16);
+            const uint32_t e = (((u >> 8) & 0xFFu) * N) >> 8;
+            const uint32_t y = div_cols(isl, p.cols_m, p.cols_l), x = isl - y * p.cols;
+            const uint32_t yn = md == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
+                              : md == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
+            const uint32_t xn = md == 2u ? (x + 1u == p.cols ? 0u : x + 1u)
+                              : md == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
+            const uint32_t nb = yn * p.cols + xn;
+            if (in_bounds(nb < p.n_islands, p.status))
+                cp_async16(&s_imm[warp][lane], &p.src[static_cast<size_t>(nb) * N + e]);
+        }
+        cp_async_commit();
+        // partial Fisher-Yates over [0, N) in direction order among the island's four lanes
+        uint32_t rr[4];
+#pragma unroll
+        for (int dd = 0; dd < 4; ++dd) rr[dd] = __shfl_sync(0xffffffffu, r, dd, 4);
+        uint32_t v[4], slot = 0;
+#pragma unroll
+        for (int dd = 0; dd < 4; ++dd) {
+            uint32_t vd = dd, vr = rr[dd];
+#pragma unroll
+            for (int e = 0; e < dd; ++e) {
+                if (rr[e] == static_cast<uint32_t>(dd)) vd = v[e];
+                if (rr[e] == rr[dd]) vr = v[e];
+            }
+            if (static_cast<uint32_t>(dd) == md) slot = vr;
+            v[dd] = vd;
+        }
+        __syncwarp();  // the table is cleared before any entry is set
+        if (ok) s_dir[warp][li][slot & 31u] = static_cast<uint8_t>(md);
+        cp_async_wait<0>();
+    }
+    __syncthreads();
+
+    const uint2 dmask = gen_mask_at(p, 0u);
+#pragma unroll 1
+    for (uint32_t un = 0; un < static_cast<uint32_t>(U); ++un) {
+        const uint32_t island = island0 + un * WARPS + warp;
+        if (island >= p.n_islands) break;  // uniform in the warp; later units lie further on
+        const uint32_t nxt = island + WARPS;
+        if (un + 1u < static_cast<uint32_t>(U) && nxt < p.n_islands)
+            cp_async16(&s_rec[warp][(un + 1u) & 1u][lane], &p.src[static_cast<size_t>(nxt) * N + lane]);
+        cp_async_commit();
+        uint4 w[1];
+        birth_draws<N>(w, p, rk, p.g0, island, lane);
+        cp_async_wait<1>();  // this island's records have landed
+        uint4 v = s_rec[warp][un & 1u][lane];
+        if (p.migrate) {
+            const uint32_t dd = s_dir[un][warp][lane];
+            const uint4 x = s_imm[un][warp * 4u + (dd & 3u)];
+            if (dd < 4u) v = x;
+        }
+        uint32_t rec[1][LW] = {{v.x, v.y, v.z, v.w}};
+        reproduce<N, SW, TS, 0, 0, 1>(rec, w, p, rk, island, lane, 0xffffffffu, p.g0, 0, dmask);
+        for (uint32_t it = 1; it < p.n_gens; ++it) {
+            birth_draws<N>(w, p, rk, p.g0 + it, island, lane);
+            reproduce<N, SW, TS, 0, 0, 1>(rec, w, p, rk, island, lane, 0xffffffffu, p.g0 + it, 0,
+                                          gen_mask_at(p, it));
+        }
+        p.dst[static_cast<size_t>(island) * N + lane] = make_uint4(rec[0][0], rec[0][1], rec[0][2], rec[0][3]);
     }
 }
 

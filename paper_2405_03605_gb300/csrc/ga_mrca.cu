@@ -2,21 +2,19 @@
 // estimation from hstrat markers, Fig. 1 caption of the paper).
 //
 // Pipeline (all on the run's stream):
-//   1. rank_kernel   : replay the curation rule over ranks 0..T-1; each site keeps the
-//                      largest rank that landed on it (atomicMax of rank + 1).
-//   2. order_kernel  : sort the occupied sites by rank (one block, S <= 256): r_1 < ... < r_m.
-//      (For T <= 16384 rank_order_kernel does both in one block, the table in shared memory.)
-//   3. pack_kernel   : gather each sampled agent's differentiae in rank order into a bit
+//   1. rank_table_kernel: the ranks the surface retains at counter T, in closed form (no
+//                      replay of ranks 0..T-1): one thread per retained rank (steady) or per
+//                      site (tilted), each rank placed at its site; then the occupied sites
+//                      sorted by rank in the same block (S <= 256): r_1 < ... < r_m.
+//   2. pack_kernel   : gather each sampled agent's differentiae in rank order into a bit
 //                      string (differentia i at bits [i*b, i*b + b)), 8 words per agent; one
 //                      warp per agent, one warp OR-reduction per packed word.
-//   4. pair_kernel   : one thread per pair (i, j), j > i, in output order; the first set bit of
+//   3. pair_kernel   : one thread per pair (i, j), j > i, in output order; the first set bit of
 //                      packed[i] ^ packed[j] gives the first mismatching rank index i*,
 //                      from which hi = r_{i*} and lo = r_{i*-K} + 1 (0 if i* <= K); with no
 //                      mismatch hi = T, lo = r_{m-K+1} + 1 (0 if m < K).
 // The pair kernel is bound by its output: 8 bytes (lo, hi) per pair, written once with
 // streaming stores.
-#include <mutex>
-
 #include "ga_device.cuh"
 #include "ga_internal.h"
 
@@ -30,7 +28,6 @@ constexpr unsigned long long kPairGrid = 152ull * 8ull;  // 8 resident blocks on
 
 
 struct MrcaLayout {
-    uint32_t *holder;  // [S]  rank + 1 held by each site (0: none)
     uint32_t *order;   // [S]  sites sorted by rank
     uint32_t *ranks;   // [S]  sorted ranks
     uint32_t *meta;    // [4]  m
@@ -39,13 +36,17 @@ struct MrcaLayout {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-MrcaLayout carve(void *scratch, uint32_t S, uint32_t n)
+// Scratch bytes of one synchronous MRCA call: order, ranks, meta, packed strings.
+size_t sync_scratch_bytes(uint32_t S, uint32_t n)
+{
+    return 2 * align_up(S * 4u, 256) + 256 + static_cast<size_t>(n) * kPackWords * 4u;
+}
+
+MrcaLayout carve(void *scratch, uint32_t S)
 {
     uint8_t *p = static_cast<uint8_t *>(scratch);
     MrcaLayout l;
     size_t off = 0;
-    l.holder = reinterpret_cast<uint32_t *>(p + off);
-    off = align_up(off + S * 4u, 256);
     l.order = reinterpret_cast<uint32_t *>(p + off);
     off = align_up(off + S * 4u, 256);
     l.ranks = reinterpret_cast<uint32_t *>(p + off);
@@ -53,59 +54,106 @@ MrcaLayout carve(void *scratch, uint32_t S, uint32_t n)
     l.meta = reinterpret_cast<uint32_t *>(p + off);
     off = align_up(off + 16u, 256);
     l.packed = reinterpret_cast<uint32_t *>(p + off);
-    (void)n;
     return l;
 }
 
-__global__ void rank_kernel(uint32_t *__restrict__ holder, uint32_t policy, uint32_t log2_sites,
-                            uint32_t sites, uint32_t T)
+// ---------------------------------------------------------------------------------------
+// Ranks retained at count T (ranks 0..T-1 deposited), without replaying them.
+//
+// Steady, S = 2^s sites: while T <= S every rank below T is held.  Otherwise let t >= 1 be
+// the epoch of rank T - 1 (bit length minus s) and P = 2^(s+t-1) its first rank.  At P the
+// surface holds exactly the ranks below P whose hanoi value is at least t - 1: the S/2 with
+// hanoi >= t (rank + 1 = 2^t q, q = 1..S/2) and the S/2 with hanoi exactly t - 1 (rank + 1 =
+// 2^(t-1) (2m + 1), m = 0..S/2-1).  Each of the c = T / 2^t - S/2 ranks of epoch t stored so
+// far (hanoi >= t: rank + 1 = 2^t (S/2 + 1), 2^t (S/2 + 2), ...) replaced the oldest remaining
+// rank of hanoi t - 1, so those m < c are gone.  Retained rank q (0 <= q < S), as rank + 1:
+// q < S/2: 2^t (q + 1); S/2 <= q < S - c: 2^(t-1) (2 (c + q - S/2) + 1); else 2^t (S/2 + 1 +
+// q - (S - c)).  A rank never moves, so its site is the closed-form site of the rank itself.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t steady_retained(uint32_t s, uint32_t T, uint32_t q)
 {
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < T;
-         t += gridDim.x * blockDim.x) {
-        const int site = curation_site(policy, log2_sites, sites, t);
-        if (site >= 0) atomicMax(&holder[site], t + 1u);
-    }
+    const uint32_t S = 1u << s;
+    if (T <= S) return q < T ? q + 1u : 0u;
+    const uint32_t t = 32u - __clz(T - 1u) - s;
+    const uint32_t half = S >> 1;
+    const uint32_t c = (T >> t) - half;
+    uint64_t r1;
+    if (q < half) r1 = static_cast<uint64_t>(q + 1u) << t;
+    else if (q < S - c) r1 = static_cast<uint64_t>(2u * (c + q - half) + 1u) << (t - 1u);
+    else r1 = static_cast<uint64_t>(half + 1u + q - (S - c)) << t;
+    return static_cast<uint32_t>(r1);
 }
 
-__global__ void order_kernel(const uint32_t *__restrict__ holder, uint32_t *__restrict__ order,
-                             uint32_t *__restrict__ ranks, uint32_t *__restrict__ meta,
-                             uint32_t sites)
+// Tilted, S sites in L = S/2 levels: site k = 2h + p.  Below the top level (h < L - 1) the
+// site holds the newest rank < T whose hanoi value is exactly h -- rank + 1 = 2^h (2m + 1) --
+// with m of parity p; the top level the newest whose hanoi value is at least L - 1 -- rank + 1
+// = 2^(L-1) m', m' >= 1 -- with m' - 1 of parity p.  Returns rank + 1, or 0 for an empty site.
+__device__ __forceinline__ uint32_t tilted_holder(uint32_t S, uint32_t T, uint32_t k)
 {
-    __shared__ uint32_t h[256];
-    release_next_grid();  // the pack kernel may start loading its agents' records
-    const uint32_t k = threadIdx.x;
-    const uint32_t mine = k < sites ? holder[k] : 0u;
-    h[k] = mine;
-    const int m = __syncthreads_count(mine != 0u);
-    if (mine != 0u) {
-        uint32_t pos = 0;
-        for (uint32_t q = 0; q < sites; ++q) pos += (h[q] != 0u && h[q] < mine) ? 1u : 0u;
-        order[pos] = k;
-        ranks[pos] = mine - 1u;
+    const uint32_t L = S >> 1, h = k >> 1, p = k & 1u;
+    if (h + 1u < L) {
+        if (h >= 32u || static_cast<uint64_t>(T) < (1ull << h)) return 0u;
+        const uint64_t mmax = (static_cast<uint64_t>(T) - (1ull << h)) >> (h + 1u);
+        const int64_t m = (mmax & 1u) == p ? static_cast<int64_t>(mmax) : static_cast<int64_t>(mmax) - 1;
+        if (m < 0) return 0u;
+        return static_cast<uint32_t>(static_cast<uint64_t>(2 * m + 1) << h);
     }
-    if (k == 0) meta[0] = static_cast<uint32_t>(m);
+    const uint32_t e = L - 1u;
+    if (e >= 32u) return 0u;
+    const int64_t mpmax = static_cast<int64_t>(static_cast<uint64_t>(T) >> e);
+    const int64_t mp = ((mpmax - 1) & 1) == static_cast<int64_t>(p) ? mpmax : mpmax - 1;
+    if (mp < 1) return 0u;
+    return static_cast<uint32_t>(static_cast<uint64_t>(mp) << e);
 }
 
-// Counters up to kFusedRankMax: the replay and the sort in one block, the site table in
-// shared memory (one launch instead of a memset and two kernels).
-constexpr uint32_t kFusedRankMax = 16384;
+// Retained entry q of the surface at count T (q < S): its site and rank + 1 (0: none).
+// Hybrid: q < S/2 are the steady half's retained ranks over the even ranks (local count
+// ceil(T/2), global rank 2 x local), q >= S/2 the tilted half's sites over the odd ranks
+// (local count floor(T/2), global rank 2 x local + 1).
+__device__ __forceinline__ uint32_t retained_entry(uint32_t policy, uint32_t s, uint32_t S,
+                                                   uint32_t T, uint32_t q, uint32_t &site)
+{
+    if (policy == kSteady) {
+        const uint32_t r1 = steady_retained(s, T, q);
+        site = r1 ? static_cast<uint32_t>(steady_site(s, r1 - 1u)) : 0u;
+        return r1;
+    }
+    if (policy == kTilted) {
+        site = q;
+        return tilted_holder(S, T, q);
+    }
+    const uint32_t half = S >> 1;
+    if (q < half) {
+        const uint32_t Te = static_cast<uint32_t>((static_cast<uint64_t>(T) + 1u) >> 1);
+        const uint32_t r1 = steady_retained(s - 1u, Te, q);
+        site = r1 ? static_cast<uint32_t>(steady_site(s - 1u, r1 - 1u)) : 0u;
+        return r1 ? 2u * (r1 - 1u) + 1u : 0u;
+    }
+    site = q;
+    const uint32_t r1 = tilted_holder(half, T >> 1, q - half);
+    return r1 ? 2u * r1 : 0u;
+}
 
-__global__ void __launch_bounds__(1024)
-rank_order_kernel(uint32_t *__restrict__ order, uint32_t *__restrict__ ranks,
+// One block of 256 threads: the retained ranks at T placed at their sites (shared memory),
+// then the occupied sites sorted by rank: order[i] = site of the i-th smallest retained rank,
+// ranks[i] = that rank, meta[0] = m.
+__global__ void __launch_bounds__(256)
+rank_table_kernel(uint32_t *__restrict__ order, uint32_t *__restrict__ ranks,
                   uint32_t *__restrict__ meta, uint32_t policy, uint32_t log2_sites,
                   uint32_t sites, uint32_t T)
 {
     __shared__ uint32_t h[256];
     release_next_grid();  // the pack kernel may start loading its agents' records
     const uint32_t k = threadIdx.x;
-    if (k < 256u) h[k] = 0u;
+    h[k] = 0u;
     __syncthreads();
-    for (uint32_t t = k; t < T; t += blockDim.x) {
-        const int site = curation_site(policy, log2_sites, sites, t);
-        if (site >= 0) atomicMax(&h[site], t + 1u);
+    if (k < sites) {
+        uint32_t site = 0;
+        const uint32_t r1 = retained_entry(policy, log2_sites, sites, T, k, site);
+        if (r1 != 0u) h[site] = r1;
     }
     __syncthreads();
-    const uint32_t mine = k < sites ? h[k] : 0u;
+    const uint32_t mine = h[k];
     const int m = __syncthreads_count(mine != 0u);
     if (mine != 0u) {
         uint32_t pos = 0;
@@ -116,21 +164,12 @@ rank_order_kernel(uint32_t *__restrict__ order, uint32_t *__restrict__ ranks,
     if (k == 0) meta[0] = static_cast<uint32_t>(m);
 }
 
-// Retained ranks at counter T, sorted (order, ranks, meta[0] = m); returns the launches made.
-int launch_rank_order(uint32_t *holder, uint32_t *order, uint32_t *ranks, uint32_t *meta,
-                      uint32_t policy, uint32_t log2_sites, uint32_t sites, uint32_t T,
-                      cudaStream_t stream)
+// Retained ranks at counter T, sorted (order, ranks, meta[0] = m): one launch for any T.
+cudaError_t launch_rank_table(uint32_t *order, uint32_t *ranks, uint32_t *meta, uint32_t policy,
+                              uint32_t log2_sites, uint32_t sites, uint32_t T, cudaStream_t stream)
 {
-    if (T <= kFusedRankMax) {
-        rank_order_kernel<<<1, 1024, 0, stream>>>(order, ranks, meta, policy, log2_sites, sites, T);
-        return 1;
-    }
-    if (cudaMemsetAsync(holder, 0, sites * sizeof(uint32_t), stream) != cudaSuccess) return 0;
-    uint32_t blocks = (T + 255u) / 256u;
-    if (blocks > 4096u) blocks = 4096u;
-    rank_kernel<<<blocks, 256, 0, stream>>>(holder, policy, log2_sites, sites, T);
-    order_kernel<<<1, 256, 0, stream>>>(holder, order, ranks, meta, sites);
-    return 2;
+    rank_table_kernel<<<1, 256, 0, stream>>>(order, ranks, meta, policy, log2_sites, sites, T);
+    return cudaGetLastError();
 }
 
 // One warp per sampled agent: lanes 0..7 hold the agent's surface words; for packed word w,
@@ -331,11 +370,11 @@ uint32_t margin(uint32_t bits)
 // Mixed counters (asynchronous runs): agents i and j may hold different counters Ti, Tj.  A
 // rank, once deposited, stays at its own site until overwritten, so the ranks retained at
 // both counters are exactly the sites whose holder tables at Ti and Tj agree.
-//   1. counter_kernel: each sampled agent's counter; Tmin and Tmax (atomicMin / atomicMax).
-//   2. base_kernel   : holder table at Tmin, replaying ranks 0 .. Tmin - 1 (as rank_kernel).
-//   3. table_kernel  : one block per sampled agent: base table plus ranks Tmin .. Ti - 1, in
-//                      shared memory; table row i (rank + 1 per site, 0: empty).
-//   4. mixed_pair_kernel: 16 x 16 pairs per block with the 32 agents' tables and surfaces in
+//   1. counter_kernel: each sampled agent's counter.
+//   2. table_kernel  : one block per sampled agent: the holder table at its counter, in
+//                      closed form as for the synchronous table; table row i (rank + 1 per
+//                      site, 0: empty).
+//   3. mixed_pair_kernel: 16 x 16 pairs per block with the 32 agents' tables and surfaces in
 //                      shared memory; one thread per pair makes two passes over the sites:
 //                      (a) the smallest common rank whose differentiae differ (hi), (b) the
 //                      K largest common ranks below it (lo = the K-th + 1).
@@ -343,36 +382,27 @@ uint32_t margin(uint32_t bits)
 constexpr int kMixTile = 16;
 
 struct MixedLayout {
-    uint32_t *meta;    // [0] Tmin, [1] Tmax
-    uint32_t *holder;  // [S] base table at Tmin
     uint32_t *cnt;     // [n] counters of the sampled agents
     uint32_t *tables;  // [n][S] rank + 1 held by each site at the agent's counter
 };
 
 size_t mixed_scratch_bytes(uint32_t S, uint32_t n)
 {
-    return 256 + align_up(S * 4u, 256) + align_up(static_cast<size_t>(n) * 4u, 256) +
-           align_up(static_cast<size_t>(n) * S * 4u, 256);
+    return align_up(static_cast<size_t>(n) * 4u, 256) + align_up(static_cast<size_t>(n) * S * 4u, 256);
 }
 
-MixedLayout carve_mixed(void *scratch, uint32_t S, uint32_t n)
+MixedLayout carve_mixed(void *scratch, uint32_t n)
 {
     uint8_t *p = static_cast<uint8_t *>(scratch);
     MixedLayout l;
-    l.meta = reinterpret_cast<uint32_t *>(p);
-    size_t off = 256;
-    l.holder = reinterpret_cast<uint32_t *>(p + off);
-    off += align_up(S * 4u, 256);
-    l.cnt = reinterpret_cast<uint32_t *>(p + off);
-    off += align_up(static_cast<size_t>(n) * 4u, 256);
-    l.tables = reinterpret_cast<uint32_t *>(p + off);
+    l.cnt = reinterpret_cast<uint32_t *>(p);
+    l.tables = reinterpret_cast<uint32_t *>(p + align_up(static_cast<size_t>(n) * 4u, 256));
     return l;
 }
 
 __global__ void counter_kernel(const uint32_t *__restrict__ pop, uint32_t record_words,
                                uint32_t n_agents, const uint32_t *__restrict__ ids, uint32_t n,
-                               uint32_t *__restrict__ cnt, uint32_t *__restrict__ meta,
-                               int *__restrict__ status)
+                               uint32_t *__restrict__ cnt, int *__restrict__ status)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -381,36 +411,23 @@ __global__ void counter_kernel(const uint32_t *__restrict__ pop, uint32_t record
     if (id >= n_agents) atomicCAS(status, GA_OK, GA_EINVAL);
     else c = pop[static_cast<size_t>(id) * record_words + 1];
     cnt[i] = c;
-    atomicMin(&meta[0], c);
-    atomicMax(&meta[1], c);
 }
 
-__global__ void base_kernel(uint32_t *__restrict__ holder, const uint32_t *__restrict__ meta,
-                            uint32_t policy, uint32_t log2_sites, uint32_t sites)
-{
-    const uint32_t T = meta[0];
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
-        const int site = curation_site(policy, log2_sites, sites, t);
-        if (site >= 0) atomicMax(&holder[site], t + 1u);
-    }
-}
-
-__global__ void table_kernel(const uint32_t *__restrict__ holder, const uint32_t *__restrict__ meta,
-                             const uint32_t *__restrict__ cnt, uint32_t *__restrict__ tables,
-                             uint32_t policy, uint32_t log2_sites, uint32_t sites)
+__global__ void __launch_bounds__(256)
+table_kernel(const uint32_t *__restrict__ cnt, uint32_t *__restrict__ tables, uint32_t policy,
+             uint32_t log2_sites, uint32_t sites)
 {
     __shared__ uint32_t h[256];
-    const uint32_t i = blockIdx.x;
-    for (uint32_t k = threadIdx.x; k < sites; k += blockDim.x) h[k] = holder[k];
+    const uint32_t i = blockIdx.x, k = threadIdx.x;
+    h[k] = 0u;
     __syncthreads();
-    const uint32_t T = cnt[i];
-    for (uint32_t t = meta[0] + threadIdx.x; t < T; t += blockDim.x) {
-        const int site = curation_site(policy, log2_sites, sites, t);
-        if (site >= 0) atomicMax(&h[site], t + 1u);
+    if (k < sites) {
+        uint32_t site = 0;
+        const uint32_t r1 = retained_entry(policy, log2_sites, sites, cnt[i], k, site);
+        if (r1 != 0u) h[site] = r1;
     }
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k < sites; k += blockDim.x)
-        tables[static_cast<size_t>(i) * sites + k] = h[k];
+    if (k < sites) tables[static_cast<size_t>(i) * sites + k] = h[k];
 }
 
 // Block (x, y): rows i in tile y, columns j in tile x (tiles below the diagonal exit).
@@ -495,9 +512,9 @@ mixed_pair_kernel(const uint32_t *__restrict__ pop, uint32_t record_words, uint3
 
 size_t mrca_scratch_bytes(const ga_run *run, uint32_t n)
 {
-    const size_t S = run->cfg.surface_sites;
-    if (run->cfg.mode != GA_SYNC) return mixed_scratch_bytes(static_cast<uint32_t>(S), n);
-    return 3 * align_up(S * 4, 256) + 256 + static_cast<size_t>(n) * kPackWords * 4 + 256;
+    const uint32_t S = run->cfg.surface_sites;
+    if (run->cfg.mode != GA_SYNC) return mixed_scratch_bytes(S, n);
+    return sync_scratch_bytes(S, n);
 }
 
 namespace {
@@ -506,23 +523,16 @@ cudaError_t launch_mrca_mixed(ga_run *run, const uint32_t *d_ids, uint32_t n, ui
                               uint32_t *d_hi, void *scratch)
 {
     const uint32_t S = run->cfg.surface_sites, b = run->cfg.differentia_bits;
-    const uint32_t policy = run->cfg.curation;
-    MixedLayout l = carve_mixed(scratch, S, n);
-    cudaError_t e = cudaMemsetAsync(l.meta, 0xFF, sizeof(uint32_t), run->stream);  // Tmin
-    if (e == cudaSuccess) e = cudaMemsetAsync(l.meta + 1, 0, sizeof(uint32_t), run->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(l.holder, 0, S * sizeof(uint32_t), run->stream);
-    if (e != cudaSuccess) return e;
+    MixedLayout l = carve_mixed(scratch, n);
     const uint32_t *pop = reinterpret_cast<const uint32_t *>(run->pop[run->cur]);
     const uint32_t rw = run->record_bytes / 4u;
     counter_kernel<<<(n + 255u) / 256u, 256, 0, run->stream>>>(pop, rw, run->n_agents, d_ids, n,
-                                                               l.cnt, l.meta, run->d_status);
-    base_kernel<<<608, 256, 0, run->stream>>>(l.holder, l.meta, policy, run->log2_sites, S);
-    table_kernel<<<n, 256, 0, run->stream>>>(l.holder, l.meta, l.cnt, l.tables, policy,
-                                             run->log2_sites, S);
+                                                               l.cnt, run->d_status);
+    table_kernel<<<n, 256, 0, run->stream>>>(l.cnt, l.tables, run->cfg.curation, run->log2_sites, S);
     const uint32_t tiles = (n + kMixTile - 1) / kMixTile;
     mixed_pair_kernel<<<dim3(tiles, tiles), kMixTile * kMixTile, 0, run->stream>>>(
         pop, rw, run->n_agents, d_ids, n, l.cnt, l.tables, S, b, margin(b), d_lo, d_hi);
-    run->launches += 4;
+    run->launches += 3;
     return cudaGetLastError();
 }
 
@@ -534,11 +544,11 @@ cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t
     if (run->cfg.mode != GA_SYNC) return launch_mrca_mixed(run, d_ids, n, d_lo, d_hi, scratch);
     const uint32_t S = run->cfg.surface_sites, b = run->cfg.differentia_bits;
     const uint32_t T = static_cast<uint32_t>(run->generation);
-    MrcaLayout l = carve(scratch, S, n);
-    const int made = launch_rank_order(l.holder, l.order, l.ranks, l.meta, run->cfg.curation,
+    MrcaLayout l = carve(scratch, S);
+    cudaError_t e0 = launch_rank_table(l.order, l.ranks, l.meta, run->cfg.curation,
                                        run->log2_sites, S, T, run->stream);
-    if (made == 0) return cudaErrorUnknown;
-    run->launches += made;
+    if (e0 != cudaSuccess) return e0;
+    run->launches += 1;
     const cudaError_t e = launch_pack_and_pairs(
         reinterpret_cast<const uint32_t *>(run->pop[run->cur]), run->record_bytes / 4u,
         run->n_agents, d_ids, n, l.order, l.ranks, l.meta, S, b, margin(b), T, l.packed, d_lo,
@@ -557,10 +567,12 @@ cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t
 //
 // The array is a file-scope __device__ variable, so every GPU that loads this library holds
 // its own copy until the process exits.  In host code the name g_mrca_fixed_scratch is only
-// a host-side stand-in for the symbol; its device address comes from cudaGetSymbolAddress,
-// taken once per device (with that device current) on the first call made on that device.
-// Every call on a device reuses the same array: the status word and the site-rank table are
-// cleared at the start of each call, the rest is fully rewritten before it is read.
+// a host-side stand-in for the symbol, never a device address; each call looks the address
+// up with cudaGetSymbolAddress, with the caller's device current, and passes it to the
+// kernels (a lookup per call stays right after a device reset reloads the module, which a
+// cached address would not).  Every call on a device reuses the same array: the status word
+// is cleared at the start of each call, the rank table and strings are fully rewritten
+// before they are read.
 // ---------------------------------------------------------------------------------------
 namespace ga {
 namespace {
@@ -568,37 +580,14 @@ namespace {
 constexpr uint32_t kFixedMaxSample = 4096;    // largest n accepted
 constexpr uint32_t kFixedMaxSites = 256;      // S * b <= 256 bits
 constexpr size_t kFixedStatusBytes = 256;     // device status word, padded
-// status, then the same layout carve() gives the per-call scratch, sized for S = 256, n = 4096
-constexpr size_t kFixedScratchBytes =
-    kFixedStatusBytes + 3 * 1024 + 256 + static_cast<size_t>(kFixedMaxSample) * kPackWords * 4 + 256;
+// status, then the layout carve() gives the per-call scratch, sized for S = 256, n = 4096:
+// 256 + 2 x 1,024 + 256 + 4,096 x 32 = 133,632 bytes
+constexpr size_t kFixedScratchBytes = kFixedStatusBytes + 2 * 1024 + 256 +
+                                      static_cast<size_t>(kFixedMaxSample) * kPackWords * 4;
 
 static __device__ __align__(256) unsigned char g_mrca_fixed_scratch[kFixedScratchBytes];
 
-std::mutex g_fixed_mutex;
-constexpr int kMaxDevices = 64;
-void *g_fixed_address[kMaxDevices] = {};
-
-// Device address of the fixed scratch for the current device (looked up once per device).
-int fixed_scratch_address(void **out)
-{
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GA_ECUDA;
-    std::lock_guard<std::mutex> lock(g_fixed_mutex);
-    if (g_fixed_address[dev] == nullptr) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_mrca_fixed_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
-            return GA_ECUDA;
-        }
-        g_fixed_address[dev] = p;
-    }
-    *out = g_fixed_address[dev];
-    return GA_OK;
-}
-
 }  // namespace
-
 }  // namespace ga
 
 extern "C" int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_bytes,
@@ -617,24 +606,29 @@ extern "C" int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_byt
     const uint32_t words = (S * b + 31u) / 32u;
     if (record_bytes != (8u + 4u * words + 15u) / 16u * 16u || n_agents == 0u) return GA_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_records) % 16u != 0u) return GA_EINVAL;
+    static_assert(kFixedStatusBytes + 2 * 1024 + 256 + kFixedMaxSample * kPackWords * 4 <=
+                      kFixedScratchBytes, "fixed scratch too small for its largest call");
 
+    // an error left pending by earlier, unrelated work on this thread is not this call's
+    cudaGetLastError();
     void *base = nullptr;
-    int rc = fixed_scratch_address(&base);
-    if (rc != GA_OK) return rc;
+    if (cudaGetSymbolAddress(&base, g_mrca_fixed_scratch) != cudaSuccess || base == nullptr) {
+        cudaGetLastError();
+        return GA_ECUDA;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int *status = static_cast<int *>(base);
-    MrcaLayout l = carve(static_cast<uint8_t *>(base) + kFixedStatusBytes, S, n);
+    MrcaLayout l = carve(static_cast<uint8_t *>(base) + kFixedStatusBytes, S);
     uint32_t log2_sites = 0;
     while ((1u << log2_sites) < S) ++log2_sites;
 
-    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess ||
-        launch_rank_order(l.holder, l.order, l.ranks, l.meta, curation, log2_sites, S,
-                          generation, st) == 0)
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return GA_ECUDA;
+    if (launch_rank_table(l.order, l.ranks, l.meta, curation, log2_sites, S, generation, st) !=
+        cudaSuccess)
         return GA_ECUDA;
     if (launch_pack_and_pairs(static_cast<const uint32_t *>(d_records), record_bytes / 4u,
                               n_agents, d_agent_ids, n, l.order, l.ranks, l.meta, S, b, margin(b),
-                              generation, l.packed, d_lo, d_hi, status, st) != cudaSuccess ||
-        cudaGetLastError() != cudaSuccess)
+                              generation, l.packed, d_lo, d_hi, status, st) != cudaSuccess)
         return GA_ECUDA;
     int device_status = GA_OK;
     if (cudaMemcpyAsync(&device_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) !=

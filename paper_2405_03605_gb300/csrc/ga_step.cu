@@ -21,6 +21,19 @@ __global__ void __launch_bounds__(kStepThreads) island_step_kernel(const StepArg
     step_block<N, SW, TS, kStepWarps, MODEL, CF>(a.r, a.rk, blockIdx.x);
 }
 
+// Units of 8 islands run by one block of the multi-unit kernel (32-agent islands, 16-byte
+// records, counters equal to the generation; step_units in ga_island.cuh).  0: not used.
+#ifndef GA_UNITS_PER_BLOCK
+#define GA_UNITS_PER_BLOCK 8
+#endif
+constexpr int kUnits = GA_UNITS_PER_BLOCK;
+
+template <int TS, int U>
+__global__ void __launch_bounds__(kStepThreads, 8) island_units_kernel(const StepArgs a)
+{
+    step_units<TS, U>(a.r, a.rk, blockIdx.x);
+}
+
 // Every record becomes the founder: trait 0, counter 0, surface word w = word 0 of
 // Philox((0, 0, w | FOUNDER << 16, run_id)); surface bits past S*b are zero.
 __global__ void founder_kernel(uint4 *__restrict__ dst, uint32_t n_agents, uint32_t q_per_rec,
@@ -55,11 +68,19 @@ __global__ void counter_check_kernel(const uint32_t *__restrict__ pop, uint32_t 
 }
 
 __global__ void curation_sites_kernel(uint32_t policy, uint32_t log2_sites, uint32_t sites,
-                                      uint32_t t0, uint32_t count, int32_t *__restrict__ out)
+                                      uint32_t t0, uint32_t count, int32_t *__restrict__ out,
+                                      uint32_t bits, uint2 *__restrict__ masks)
 {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += gridDim.x * blockDim.x)
-        out[i] = curation_site(policy, log2_sites, sites, t0 + i);
+         i += gridDim.x * blockDim.x) {
+        const int site = curation_site(policy, log2_sites, sites, t0 + i);
+        out[i] = site;
+        if (masks) {  // sites * bits <= 64: the deposit's bits within surface words 0 and 1
+            const uint32_t pos = site >= 0 ? static_cast<uint32_t>(site) * bits : 0u;
+            const uint32_t m = site >= 0 ? ((1u << bits) - 1u) << (pos & 31u) : 0u;
+            masks[i] = make_uint2(pos < 32u ? m : 0u, pos < 32u ? 0u : m);
+        }
+    }
 }
 
 namespace {
@@ -198,6 +219,10 @@ RunParams run_params(const ga_run *run, const void *src, void *dst, uint32_t g0,
     r.effect_scale = static_cast<float>(run->cfg.effect_scale);
     r.gen_sites_left = kSiteTableCap - static_cast<uint32_t>(g0 - run->sites_base);
     r.status = run->d_status;
+    r.gen_masks = run->d_masks + (g0 - run->sites_base);
+    const uint32_t b = run->cfg.differentia_bits;
+    r.dif_mask = (1u << b) - 1u;
+    r.dif_rep = b == 1u ? 0xFFFFFFFFu : b == 2u ? 0x55555555u : b == 4u ? 0x11111111u : 0x01010101u;
     return r;
 }
 
@@ -240,6 +265,18 @@ cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t
 {
     const bool uniform = run->cfg.mode == GA_SYNC && run->counters_uniform &&
                          run->cfg.tournament_size == 5;
+    if (kUnits > 0 && uniform && run->cfg.island_size == 32 && run->surface_words <= 2 &&
+        run->cfg.model == GA_MODEL_TRAIT) {
+        StepArgs a;
+        a.r = run_params(run, src, dst, g0, n_gens, migrate);
+        a.rk = round_keys(Key{static_cast<uint32_t>(run->cfg.seed),
+                              static_cast<uint32_t>(run->cfg.seed >> 32)});
+        const uint32_t per_block = kStepWarps * static_cast<uint32_t>(kUnits > 0 ? kUnits : 1);
+        const uint32_t blocks = (run->n_islands + per_block - 1) / per_block;
+        island_units_kernel<5, (kUnits > 0 ? kUnits : 1)><<<blocks, kStepThreads, 0, stream>>>(a);
+        run->launches += 1;
+        return cudaGetLastError();
+    }
     StepKernel k =
         uniform ? pick_uniform(run->cfg.island_size, run->surface_words, run->cfg.model) : nullptr;
     if (!k)
@@ -260,21 +297,25 @@ cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t
 
 cudaError_t launch_site_table(ga_run *run, uint32_t g0, uint32_t count, cudaStream_t stream)
 {
-    const cudaError_t e = launch_curation_sites(run->cfg.curation, run->cfg.surface_sites, g0,
-                                                count, run->d_sites, stream);
+    const bool masks = run->surface_words <= 2u;
+    const cudaError_t e = launch_curation_sites(
+        run->cfg.curation, run->cfg.surface_sites, g0, count, run->d_sites, stream,
+        run->cfg.differentia_bits, masks ? run->d_masks : nullptr);
     run->launches += 1;
     return e;
 }
 
 cudaError_t launch_curation_sites(uint32_t policy, uint32_t sites, uint32_t t0, uint32_t count,
-                                  int32_t *d_sites, cudaStream_t stream)
+                                  int32_t *d_sites, cudaStream_t stream, uint32_t bits,
+                                  uint2 *d_masks)
 {
     if (count == 0) return cudaSuccess;
     uint32_t s = 0;
     while ((1u << s) < sites) ++s;
     uint32_t blocks = (count + 255u) / 256u;
     if (blocks > 8192u) blocks = 8192u;
-    curation_sites_kernel<<<blocks, 256, 0, stream>>>(policy, s, sites, t0, count, d_sites);
+    curation_sites_kernel<<<blocks, 256, 0, stream>>>(policy, s, sites, t0, count, d_sites, bits,
+                                                      d_masks);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ EXPORTED = (
     "ga_curation_sites", "ga_mrca_bounds_noalloc", "ga_batch_create", "ga_batch_add",
     "ga_batch_remove", "ga_batch_size", "ga_batch_step", "ga_batch_sync",
     "ga_batch_launch_count", "ga_batch_autotune", "ga_batch_class_warps", "ga_batch_destroy",
-    "ga_async_window",
+    "ga_async_window", "ga_int_peak",
 )
 
 
@@ -99,6 +99,7 @@ def load_library(path=LIB_PATH):
         "ga_batch_class_warps": ([vp, u32, C.POINTER(u32), C.POINTER(u32)], C.c_int),
         "ga_batch_destroy": ([vp], C.c_int),
         "ga_async_window": ([vp, u32], C.c_int),
+        "ga_int_peak": ([u32, u32, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -304,9 +305,21 @@ def curation_sites(policy, surface_sites, t0, count, stream=None):
 def mrca_bounds_noalloc(records_ptr, record_bytes, n_agents, curation, surface_sites,
                         differentia_bits, generation, ids, lo, hi, stream=None):
     """ga_mrca_bounds_noalloc: MRCA bounds for callers that cannot allocate device memory.
-    records_ptr: device address of the canonical records; ids, lo, hi: device tensors with
-    32-bit elements, caller-allocated.  Synchronous; raises GaError on failure."""
+    records_ptr: device address of the canonical records; ids, lo, hi: contiguous device
+    tensors with 32-bit elements, caller-allocated, lo and hi distinct and holding at least
+    n (n - 1) / 2 elements each (ValueError otherwise).  Synchronous; raises GaError when the
+    library reports a failure."""
     import torch
+    n = ids.numel()
+    pairs = n * (n - 1) // 2
+    for name, t, need in (("ids", ids, n), ("lo", lo, pairs), ("hi", hi, pairs)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
+                and t.element_size() == 4):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of 4-byte elements")
+        if t.numel() < need:
+            raise ValueError(f"{name} holds {t.numel()} elements, {need} needed")
+    if lo.data_ptr() == hi.data_ptr():
+        raise ValueError("lo and hi must be distinct tensors")
     lib = load_library()
     f = lib.ga_mrca_bounds_noalloc
     f.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
@@ -314,8 +327,22 @@ def mrca_bounds_noalloc(records_ptr, record_bytes, n_agents, curation, surface_s
     f.restype = C.c_int
     st = (stream or torch.cuda.current_stream()).cuda_stream
     _check(f(records_ptr, record_bytes, n_agents, curation, surface_sites, differentia_bits,
-             generation, ids.data_ptr(), ids.numel(), lo.data_ptr(), hi.data_ptr(), st or None),
+             generation, ids.data_ptr(), n, lo.data_ptr(), hi.data_ptr(), st or None),
            "ga_mrca_bounds_noalloc")
+
+
+PEAK_LOP3, PEAK_IMAD, PEAK_MIX = 0, 1, 2
+
+
+def int_peak(kind, iters=2048, stream=None):
+    """ga_int_peak: (operations per second, seconds) of one timed launch of the integer-pipe
+    probe on the current device."""
+    import torch
+    rate, sec = C.c_double(), C.c_double()
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(load_library().ga_int_peak(kind, iters, st or None, C.byref(rate), C.byref(sec)),
+           "ga_int_peak")
+    return rate.value, sec.value
 
 
 class Batch:

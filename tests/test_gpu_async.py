@@ -285,3 +285,57 @@ def test_reset_and_load_empty_the_buffers(sites):
     o.load(first, 30)
     o.step_async(20, window=4)
     assert_same(g.snapshot(), o.snapshot(), 16)
+
+
+@pytest.mark.parametrize("window", [1, 4])  # one-generation kernel, multi-generation kernel
+def test_reserved_counter_is_refused_and_reported(window):
+    """Counter 2^32 - 1 marks an empty 16-byte buffer, so the asynchronous modes keep it out
+    of every valid run: ga_load refuses it (GA_EINVAL), and a birth that would produce it
+    (parents at 2^32 - 2) leaves GA_ESTATE in the status word for the next ga_sync.  The
+    synchronous mode has no buffers and accepts it."""
+    from paper_2405_03605_gb300 import ga
+    shape = RunShape(rows=2, cols=3, island_size=16, seed=12, mode=ASYNC, async_window=window)
+    g = gpu_run(shape)
+    rec = g.snapshot()
+    rec[:, 4:8] = np.array([0xFFFFFFFF], np.uint32).view(np.uint8)
+    with pytest.raises(ga.GaError) as e:
+        g.load(rec, 0)
+    assert e.value.code == -1
+    rec[:, 4:8] = np.array([0xFFFFFFFE], np.uint32).view(np.uint8)
+    g.load(rec, 0)
+    g.step(window)
+    with pytest.raises(ga.GaError) as e:
+        g.sync()
+    assert e.value.code == -5
+    g.sync()  # the status word was read and cleared
+    s = gpu_run(shape.with_(mode=SYNC))
+    rec[:, 4:8] = np.array([0xFFFFFFFF], np.uint32).view(np.uint8)
+    s.load(rec, 0)
+    s.step(2)
+    s.sync()
+
+
+@pytest.mark.parametrize("S,b,policy,t_lo,t_hi", [
+    (64, 1, STEADY, 70000, 73000),
+    (32, 8, TILTED, 100000, 100500),
+    (256, 1, HYBRID, 16000, 40000),
+])
+def test_mixed_mrca_large_counters_match_oracle(S, b, policy, t_lo, t_hi):
+    """Counters past 16,384 spread over a range, sparse random surfaces (first mismatches
+    anywhere in the shared ranks): the GPU's per-agent tables (closed form) and the oracle's
+    (replay) give the same bounds on every pair."""
+    shape = RunShape(rows=4, cols=8, island_size=32, surface_sites=S, differentia_bits=b,
+                     curation=policy, mode=ASYNC)
+    rng = np.random.default_rng(S + b)
+    rb = oracle.record_bytes(S, b)
+    rec = np.zeros((shape.n_agents, rb), np.uint8)
+    on = rng.random((shape.n_agents, S * b)) < rng.uniform(0.001, 0.05, (shape.n_agents, 1))
+    rec[:, 8:8 + S * b // 8] = np.packbits(on, axis=1, bitorder="little")
+    rec[:, 4:8] = rng.integers(t_lo, t_hi, shape.n_agents).astype(np.uint32).view(np.uint8).reshape(-1, 4)
+    g = gpu_run(shape)
+    g.load(rec, 0)
+    ids = rng.permutation(shape.n_agents)[:300].astype(np.uint32)
+    lo, hi = g.mrca_bounds(ids)
+    elo, ehi = oracle.mrca_bounds_mixed(rec, ids, policy, S, b)
+    assert np.array_equal(hi, ehi), np.nonzero(hi != ehi)[0][:5]
+    assert np.array_equal(lo, elo), np.nonzero(lo != elo)[0][:5]

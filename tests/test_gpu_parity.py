@@ -233,3 +233,22 @@ def test_full_grid_first_generations():
     lo, hi = g.mrca_bounds(ids)
     elo, ehi = o.mrca_bounds(ids)
     assert np.array_equal(lo, elo) and np.array_equal(hi, ehi)
+
+
+@pytest.mark.parametrize("shape", [
+    RunShape(rows=16, cols=16, island_size=32, surface_sites=64, differentia_bits=1,
+             curation=STEADY, seed=101, run_id=1),
+    RunShape(rows=16, cols=16, island_size=32, surface_sites=32, differentia_bits=8,
+             curation=TILTED, seed=102, run_id=2),
+], ids=["steady64x1", "tilted32x8"])
+def test_benchmark_depth_10000_generations(shape):
+    """A 16x16 torus for 10,000 generations -- the depth the benchmark runs, where steady
+    curation reaches epoch 8 -- compared with the oracle on every agent, then the MRCA bounds
+    of 2,000 sampled agents at T = 10,000 compared pair by pair (8,192 agents coalesce within
+    a few dozen generations, so most pairs share the newest retained ranks)."""
+    g, o, got, exp = run_both(shape, 10000, chunks=[4096, 4096, 1808])
+    assert_same(got, exp, 32)
+    ids = sample_agent_ids(shape.n_agents, 2000, seed=8)
+    lo, hi = g.mrca_bounds(ids)
+    elo, ehi = o.mrca_bounds(ids)
+    assert np.array_equal(lo, elo) and np.array_equal(hi, ehi)

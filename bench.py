@@ -31,6 +31,12 @@ if ROOT not in sys.path:
 
 METRIC = "agent-gens/sec @16.8M agents on 1 GB300; % roofline; batched vs serial"
 UNIT = "agent-gens/s"
+# legs of the default line: main (the headline, 16.8M agents), e2e (the same job through the
+# public API with host buffers), batch, async, resident (the 32x32 torus), peak (integer-pipe
+# probe), variants (surface variants), treatments (the paper's float treatments), serve
+# (1,000-request trace), cpu-baseline (the oracle on the host cores)
+LEGS = ("main", "e2e", "batch", "async", "resident", "peak", "variants", "treatments", "serve",
+        "cpu-baseline")
 
 
 def parse_args():
@@ -47,18 +53,23 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--batch-runs", type=int, default=256)
     p.add_argument("--batch-gens", type=int, default=2000)
-    p.add_argument("--no-batch", action="store_true")
-    p.add_argument("--serve", action="store_true")
-    p.add_argument("--serve-requests", type=int, default=200)
-    p.add_argument("--variants", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=1000)
     p.add_argument("--variant-gens", type=int, default=1000)
-    p.add_argument("--paper-treatments", action="store_true")
     p.add_argument("--treatment-gens", type=int, default=10000)
-    p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-async", action="store_true")
     p.add_argument("--async-gens", type=int, default=2000)
-    p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    p.add_argument("--resident-gens", type=int, default=1000)
+    p.add_argument("--legs", default="all",
+                   help="comma list of: " + ",".join(LEGS) + " (default all); the headline "
+                        "value comes from 'main'")
+    for leg in LEGS:
+        p.add_argument(f"--no-{leg}", action="store_true", help=f"drop the {leg} leg")
+    a = p.parse_args()
+    chosen = set(LEGS) if a.legs == "all" else set(x.strip() for x in a.legs.split(",") if x.strip())
+    unknown = chosen - set(LEGS)
+    if unknown:
+        p.error(f"unknown legs: {sorted(unknown)}")
+    a.run = {leg: leg in chosen and not getattr(a, "no_" + leg.replace("-", "_")) for leg in LEGS}
+    return a
 
 
 def dist_info():
@@ -147,12 +158,19 @@ class Clocks:
                 "samples": len(rows), "reasons": reasons}
 
 
-# DRAM bytes (read + write) of one island_step_kernel<32,2,5,0,0> launch on the 512x1024x32 grid:
-# dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of this kernel build, and
-# its warp-instructions per island-generation (smsp__inst_executed.sum / 524,288 islands).
-ISLAND_STEP_TRAFFIC = {"kernel": "island_step_kernel<32,2,5,0,0>", "bytes": 494.5e6,
-                       "inst_per_island_gen": 98.63e6 / 524288,
+# Counters of one launch of the island step on the 512x1024x32 grid (migration every
+# generation), from ncu captures of this kernel build (profiles/): DRAM bytes read + written,
+# warp-instructions per island-generation (smsp__inst_executed.sum / islands), ALU-pipe
+# warp-instructions per island-generation (sm__inst_executed_pipe_alu.sum / islands; each
+# occupies the ALU pipe two cycles) and FMA-heavy pipe cycles per island-generation
+# (sm__pipe_fmaheavy_cycles_active.sum / islands).
+ISLAND_STEP_TRAFFIC = {"kernel": "island_units_kernel<5,8>", "bytes": 449.3e6,
+                       "inst_per_island_gen": 44564480 / 262144,
+                       "alu_inst_per_island_gen": 18513920 / 262144,
+                       "fma_cycles_per_island_gen": 33488896 / 262144,
                        "rows": 512, "cols": 1024, "island_size": 32}
+# warp-instructions per island-generation of the resident kernel on the 32x32 torus (ncu)
+RESIDENT_INST = {"kernel": "resident_kernel<32,5,0,4>", "inst_per_island_gen": None}
 
 
 def aggregate_replicas(elapsed_ms, agent_gens, world, device="cpu"):
@@ -255,6 +273,75 @@ def run_ours(args, rank, world, local):
             dist.barrier()
 
     shs = shapes(args, rank)
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {**workload_config(args, shs[0]),
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}}
+    launches = 0
+    clk = None
+    if args.run["main"]:
+        main, launches, clk = measure_main(args, shs, rank, world, local, barrier)
+        line.update(main)
+
+    extra = {}
+    if args.run["e2e"]:
+        ids_h = sample_agent_ids(shs[0].n_agents, args.sample, seed=42)
+        extra["e2e"] = measure_e2e(args, shs, ids_h, world)
+    if args.run["batch"]:
+        extra["batched_vs_serial"] = measure_batch(args, rank)
+    if rank == 0:
+        if args.run["peak"]:
+            extra["int_peak"] = measure_peak(args)
+        if args.run["resident"]:
+            extra["resident"] = measure_resident(args, extra.get("int_peak"))
+        if args.run["async"]:
+            extra["async"] = measure_async(args)
+        if args.run["variants"]:
+            extra["variants"] = measure_variants(args)
+        if args.run["treatments"]:
+            extra["paper_treatments"] = measure_treatments(args)
+        if args.run["serve"]:
+            extra["serving"] = measure_serve(args)
+    if rank != 0:
+        return
+    issue = line.get("issue_roofline")
+    if issue is not None:
+        mhz = (clk or {}).get("sm_mhz") or 2070.0  # sampled median SM clock, else the maximum
+        issue["peak"] = issue["sms"] * 4 * mhz * 1e6
+        issue["frac"] = issue["achieved"] / issue["peak"]
+        issue["clock_mhz"] = mhz
+        # pipes: the ALU pipe takes a warp-instruction every two cycles per sub-partition (its
+        # measured ceiling is the LOP3 stream of the integer probe), the FMA-heavy pipe is busy
+        # the measured cycles per island-generation
+        rate = issue["island_gens_per_s"]
+        alu = ISLAND_STEP_TRAFFIC["alu_inst_per_island_gen"] * rate
+        fma = ISLAND_STEP_TRAFFIC["fma_cycles_per_island_gen"] * rate
+        subparts = issue["sms"] * 4 * mhz * 1e6
+        issue["alu_pipe_frac"] = alu * 2 / subparts
+        issue["fma_pipe_frac"] = fma / subparts
+        peak = extra.get("int_peak")
+        if peak:
+            issue["alu_vs_measured_lop3_stream"] = alu / peak["lop3"]["warp_instr_per_s"]
+    cpu = None
+    if args.run["cpu-baseline"] and world == 1:
+        cpu = cpu_baseline(args, shs[0], args.cpu_seconds)
+    line.update(extra)
+    line["gpu_launches"] = launches
+    line["cpu_baseline"] = cpu
+    line["clocks"] = clk
+    line.setdefault("e2e", None)
+    print(json.dumps(line), flush=True)
+
+
+def measure_main(args, shs, rank, world, local, barrier):
+    """The headline: for each treatment, reset to the founder population, --gens generations,
+    MRCA bounds over --sample agents; --warmup untimed steps, then --steps timed."""
+    import numpy as np
+    import torch
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import sample_agent_ids
+
     stream = torch.cuda.Stream()
     runs = [ga.Run(s, stream=stream) for s in shs]
     n = args.sample
@@ -340,43 +427,16 @@ def run_ours(args, rank, world, local):
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     issue = None
     if same_shape:
-        inst_rate = ISLAND_STEP_TRAFFIC["inst_per_island_gen"] * shs[0].n_islands / avg_launch_s
+        island_gens = shs[0].n_islands / avg_launch_s
+        inst_rate = ISLAND_STEP_TRAFFIC["inst_per_island_gen"] * island_gens
         issue = {"bound": "alu", "unit": "warp-instr/s", "achieved": inst_rate,
                  "per_unit": ISLAND_STEP_TRAFFIC["inst_per_island_gen"],
                  "unit_of_work": "island-generation (ncu smsp__inst_executed.sum of this build)",
-                 "sms": n_sm}
-
-    e2e = None
-    if not args.no_e2e:
-        e2e = measure_e2e(args, shs, ids_h, world)
-    batched = None
-    if not args.no_batch:
-        batched = measure_batch(args, rank)
-    served = measure_serve(args) if args.serve and rank == 0 else None
-    variants = measure_variants(args) if args.variants and rank == 0 else None
-    treatments = measure_treatments(args) if args.paper_treatments and rank == 0 else None
-    asynchronous = measure_async(args) if not args.no_async and rank == 0 else None
-
+                 "sms": n_sm, "island_gens_per_s": island_gens}
     for r in runs:
         r.close()
-
-    if rank != 0:
-        return
-    if issue is not None:
-        mhz = (clk or {}).get("sm_mhz") or 2070.0  # sampled median SM clock, else the maximum
-        issue["peak"] = issue["sms"] * 4 * mhz * 1e6
-        issue["frac"] = issue["achieved"] / issue["peak"]
-        issue["clock_mhz"] = mhz
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(args, shs[0], args.cpu_seconds)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {**workload_config(args, shs[0]),
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+    main = {
+        "value": value, "ms_per_step": elapsed_ms / args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": ISLAND_STEP_TRAFFIC["kernel"],
@@ -387,19 +447,78 @@ def run_ours(args, rank, world, local):
         "mrca": {"ms_per_run": mrca_ms, "pairs": pairs, "bytes_written": 8 * pairs,
                  "achieved": 8 * pairs / (mrca_ms / 1000.0) / 1e9, "peak": peak, "unit": "GB/s",
                  "frac": 8 * pairs / (mrca_ms / 1000.0) / 1e9 / peak,
-                 "note": "every MRCA kernel of the call (replay and rank sort, pack, pairs); bound by the (lo, hi) output writes"},
+                 "note": "every MRCA kernel of the call (closed-form rank table, pack, pairs); "
+                         "bound by the (lo, hi) output writes"},
         "treatment_contrast": contrast,
-        "batched_vs_serial": batched,
-        **({"serving": served} if served is not None else {}),
-        **({"variants": variants} if variants is not None else {}),
-        **({"paper_treatments": treatments} if treatments is not None else {}),
-        **({"async": asynchronous} if asynchronous is not None else {}),
-        "gpu_launches": launches,
-        "e2e": e2e,
-        "cpu_baseline": cpu,
-        "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    return main, launches, clk
+
+
+def measure_peak(args):
+    """Integer-pipe probe (ga_int_peak): operations and warp-instructions per second of
+    dependence-free LOP3, IMAD.WIDE and Philox-round streams, next to the nominal issue limit
+    (4 warp-instructions per clock per SM)."""
+    import torch
+    from paper_2405_03605_gb300 import ga
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = {"nominal_issue_warp_instr_per_s_at_2070mhz": n_sm * 4 * 2070e6}
+    for name, kind in (("lop3", ga.PEAK_LOP3), ("imad_wide", ga.PEAK_IMAD), ("philox_mix", ga.PEAK_MIX)):
+        rate, sec = ga.int_peak(kind, iters=4096)
+        out[name] = {"ops_per_s": rate, "warp_instr_per_s": rate / 32.0, "seconds": sec}
+    return out
+
+
+def measure_resident(args, peak):
+    """The 32x32 torus of 32-agent islands (32,768 agents, 16-byte records, migration every
+    generation) for --resident-gens generations from the founder population: resident (one
+    cooperative launch, islands in registers, migrants through mailboxes) and streamed (one
+    launch per generation), CUDA events on the run's stream, end states compared."""
+    import torch
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import SMALL_TORUS
+
+    gens = args.resident_gens
+    stream = torch.cuda.Stream()
+    out = {"workload": "32x32 torus x 32 agents (32,768 agents), 16 B records, migration every "
+                       f"generation, {gens} gens", "generations": gens}
+    snaps = {}
+    for name, mode in (("resident", ga.RESIDENT_ON), ("streamed", ga.RESIDENT_OFF)):
+        r = ga.Run(SMALL_TORUS, stream=stream)
+        r.resident_policy(mode)
+        r.step(gens)  # warm-up
+        r.reset()
+        times = []
+        for _ in range(3):
+            r.reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r.step(gens)
+            e1.record(stream)
+            r.sync()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        with torch.cuda.stream(stream):
+            snaps[name] = r.snapshot_device()
+        stream.synchronize()
+        out[name] = {"agent_gens_per_s": SMALL_TORUS.n_agents * gens / (ms / 1000.0),
+                     "us_per_gen": ms * 1000.0 / gens, "launches": r.launches}
+        r.close()
+    with torch.cuda.stream(stream):
+        out["identical"] = bool(torch.equal(snaps["resident"], snaps["streamed"]))
+    stream.synchronize()
+    out["resident_vs_streamed"] = (out["resident"]["agent_gens_per_s"] /
+                                   out["streamed"]["agent_gens_per_s"])
+    per = RESIDENT_INST["inst_per_island_gen"]
+    if per:
+        rate = per * SMALL_TORUS.n_islands * gens / (out["resident"]["us_per_gen"] * 1e-6 * gens)
+        n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        issue = {"kernel": RESIDENT_INST["kernel"], "inst_per_island_gen": per,
+                 "warp_instr_per_s": rate, "nominal_issue_frac": rate / (n_sm * 4 * 2070e6)}
+        if peak:
+            issue["vs_measured_lop3_stream"] = rate / peak["lop3"]["warp_instr_per_s"]
+            issue["vs_measured_philox_mix"] = rate / peak["philox_mix"]["warp_instr_per_s"]
+        out["issue"] = issue
+    return out
 
 
 def measure_batch(args, rank):
@@ -593,6 +712,12 @@ def measure_async(args):
                 "median_counter_over_generation": med / gens,
                 "mean_mrca_depth": depth, "mrca_ms": e1.elapsed_time(e2)}
             r.close()
+    # the asynchronous figure: window 1, where no island gets more than a generation ahead of
+    # another (window 16 lets lineages run ahead of the schedule: reported, not the figure)
+    w1 = [out["window1_adaptive"], out["window1_purifying"]]
+    out["agent_gens_per_s"] = statistics.mean(x["agent_gens_per_s"] for x in w1)
+    out["median_counter_over_generation"] = max(x["median_counter_over_generation"] for x in w1)
+    out["figure"] = "window 1, mean of both treatments; drift = largest median counter / generation"
     return out
 
 

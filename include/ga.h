@@ -45,7 +45,7 @@ extern "C" {
 #define GA_EINVAL (-1)       /* invalid argument or configuration                        */
 #define GA_ENOMEM (-2)       /* device allocation failed, or caller workspace too small  */
 #define GA_ECUDA (-3)        /* a CUDA runtime call or kernel launch failed              */
-#define GA_ETIMEOUT (-4)     /* a bounded device-side wait expired                       */
+#define GA_ETIMEOUT (-4)     /* a bounded device-side wait expired (resident stepping)   */
 #define GA_ESTATE (-5)       /* device state does not allow the request (e.g. counters of
                                 sampled agents differ, so no common rank table exists)   */
 #define GA_EUNSUPPORTED (-6) /* valid configuration with no compiled kernel for it       */
@@ -108,7 +108,8 @@ int ga_record_bytes(const ga_config *cfg, uint32_t *bytes);
 
 /* Bytes of device workspace a run of cfg needs (two population buffers plus a header; in the
    asynchronous modes also four send buffers per island: 16 bytes each for 16-byte records,
-   16 + record_bytes otherwise). */
+   16 + record_bytes otherwise; for synchronous runs of at most 8,192 islands with 16-byte
+   records also the resident-stepping mailboxes, 128 bytes per island plus 256). */
 int ga_workspace_bytes(const ga_config *cfg, size_t *bytes);
 
 /*
@@ -163,6 +164,38 @@ int ga_migrate_policy(ga_run *run, uint32_t per_neighbor, uint32_t every_k);
  * Errors: GA_EINVAL (window out of range), GA_ESTATE (run not in an asynchronous mode).
  */
 int ga_async_window(ga_run *run, uint32_t window);
+
+/*
+ * Resident stepping (Sec. 2: each processor keeps its population in place and exchanges only
+ * migrants with its neighbours).  A synchronous run whose islands all fit on the GPU at once
+ * can step a whole chunk of up to 4,096 generations in one cooperative launch: every island
+ * stays in registers, and on each migration generation an island pushes the member each
+ * neighbour draws into that neighbour's mailbox (one 16-byte atomic write) and reads its own
+ * four mailboxes, waiting until each holds the record of the current generation.  Results are
+ * bit-identical to the streamed launches.  Eligible: GA_SYNC, 16-byte records, island sizes
+ * 8 to 64, counters equal to the generation, at most 8,192 islands, and a grid that the
+ * device can hold resident; the mailboxes (128 bytes per island) are part of the workspace of
+ * such runs.
+ *   GA_RESIDENT_AUTO  (default) resident launches whenever eligible;
+ *   GA_RESIDENT_OFF   one launch per migration interval, the population streamed;
+ *   GA_RESIDENT_ON    resident launches; ga_step returns GA_EUNSUPPORTED if not eligible.
+ * wait_limit_us bounds every wait for a mailbox (wall clock, default 1,000,000 = 1 s): when
+ * it runs out the launch records GA_ETIMEOUT, every block leaves at its next migration
+ * generation, the population is undefined, and the next ga_sync returns GA_ETIMEOUT (the
+ * run can then be reset or loaded and stepped again).  Errors: GA_EINVAL (mode, limit 0).
+ */
+#define GA_RESIDENT_AUTO 0u
+#define GA_RESIDENT_OFF 1u
+#define GA_RESIDENT_ON 2u
+int ga_resident_policy(ga_run *run, uint32_t mode, uint32_t wait_limit_us);
+
+/*
+ * Fault injection for testing the bounded waits above (the paper has no counterpart): in
+ * resident launches, island `island` never pushes its emigrants, so its four neighbours wait
+ * for mailboxes that nothing fills until their limit runs out.  0xFFFFFFFF (the default)
+ * turns it off.  Errors: GA_EINVAL (island out of range).
+ */
+int ga_inject_lost_migrants(ga_run *run, uint32_t island);
 
 /*
  * Enqueue n_gens generations on the run's stream (Sec. 2 generational cycle, halting after
@@ -256,11 +289,14 @@ typedef struct ga_batch ga_batch;
    and owns).  Errors: GA_EINVAL, GA_ENOMEM, GA_ECUDA. */
 int ga_batch_create(void *stream, ga_batch **out);
 
-/* Add a run (synchronises the run's stream and the batch's stream).  GA_EINVAL if it is
-   already a member of this or another batch. */
+/* Add a run.  The batch's stream is ordered after the work already queued on the run's
+   stream (a device-side wait; the host does not block).  GA_EINVAL if it is already a member
+   of this or another batch. */
 int ga_batch_add(ga_batch *batch, ga_run *run);
 
-/* Remove a member run (synchronises the batch's stream; the run keeps its state). */
+/* Remove a member run (the run keeps its state).  Work queued on the run's own stream
+   afterwards, ga_destroy's wait included, is ordered after the batch launches already queued
+   (a device-side wait; the host does not block). */
 int ga_batch_remove(ga_batch *batch, ga_run *run);
 
 /* Number of member runs. */

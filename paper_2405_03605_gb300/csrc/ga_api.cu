@@ -71,11 +71,13 @@ size_t population_bytes(const ga_config *c)
 
 size_t buffer_stride(const ga_config *c) { return align_up(population_bytes(c), 256); }
 
-// Workspace: header, two population buffers, then (asynchronous modes) the send buffers.
+// Workspace: header, two population buffers, then the send buffers (asynchronous modes) or
+// the resident mailboxes (synchronous runs small enough to step resident).
 size_t workspace_need(const ga_config *c)
 {
     size_t need = ga::kHeaderBytes + 2 * buffer_stride(c);
     if (c->mode != GA_SYNC) need += ga::async_state_bytes(c->rows * c->cols, record_bytes_of(c));
+    else need += ga::resident_state_bytes(c->rows * c->cols, record_bytes_of(c));
     return need;
 }
 
@@ -110,12 +112,28 @@ int step_run(ga_run *run, uint32_t n_gens, cudaStream_t stream)
 {
     if (run->cfg.mode != GA_SYNC) return async_step(run, n_gens, stream);
     if (run->generation + n_gens > 0xFFFFFFFFull) return GA_EINVAL;
+    // resident launches: one cooperative launch per chunk of the site table
+    bool resident = false;
+    if (n_gens > 0 && run->resident_mode != GA_RESIDENT_OFF) {
+        const bool wanted = run->resident_mode == GA_RESIDENT_ON || run->n_islands <= kResidentAutoIslands;
+        resident = wanted && resident_possible(run, nullptr);
+        if (run->resident_mode == GA_RESIDENT_ON && !resident) return GA_EUNSUPPORTED;
+    }
     while (n_gens > 0) {
         // curation sites of the next chunk of generations, computed on the device once
         const uint32_t chunk = n_gens < kSiteTableCap ? n_gens : kSiteTableCap;
         int rc = cuda_rc(launch_site_table(run, static_cast<uint32_t>(run->generation), chunk, stream));
         if (rc != GA_OK) return rc;
         run->sites_base = run->generation;
+        if (resident) {
+            rc = cuda_rc(launch_resident(run, run->pop[run->cur], run->pop[run->cur ^ 1],
+                                         static_cast<uint32_t>(run->generation), chunk, stream));
+            if (rc != GA_OK) return rc;
+            run->cur ^= 1;
+            run->generation += chunk;
+            n_gens -= chunk;
+            continue;
+        }
         uint32_t left = chunk;
         while (left > 0) {
             const uint64_t g = run->generation;
@@ -230,6 +248,13 @@ int ga_create(const ga_config *cfg, void *workspace, size_t workspace_bytes, ga_
     run->d_flag = reinterpret_cast<int *>(base + ga::kStatusBytes / 2);
     run->d_sites = reinterpret_cast<int32_t *>(base + ga::kStatusBytes);
     run->d_masks = reinterpret_cast<uint2 *>(base + ga::kMaskOffset);
+    run->resident_state = nullptr;
+    if (cfg->mode == GA_SYNC &&
+        ga::resident_state_bytes(run->n_islands, run->record_bytes) != 0)
+        run->resident_state = base + ga::kHeaderBytes + 2 * buffer_stride(cfg);
+    run->resident_mode = GA_RESIDENT_AUTO;
+    run->resident_wait_us = 1000000u;
+    run->drop_island = 0xFFFFFFFFu;
     run->sites_base = 0;
     run->pop[0] = base + ga::kHeaderBytes;
     run->pop[1] = base + ga::kHeaderBytes + buffer_stride(cfg);
@@ -275,6 +300,21 @@ int ga_async_window(ga_run *run, uint32_t window)
     if (!run || window == 0u || window > GA_ASYNC_MAX_WINDOW) return GA_EINVAL;
     if (run->cfg.mode == GA_SYNC) return GA_ESTATE;
     run->async_window = window;
+    return GA_OK;
+}
+
+int ga_resident_policy(ga_run *run, uint32_t mode, uint32_t wait_limit_us)
+{
+    if (!run || mode > GA_RESIDENT_ON || wait_limit_us == 0u) return GA_EINVAL;
+    run->resident_mode = mode;
+    run->resident_wait_us = wait_limit_us;
+    return GA_OK;
+}
+
+int ga_inject_lost_migrants(ga_run *run, uint32_t island)
+{
+    if (!run || (island != 0xFFFFFFFFu && island >= run->n_islands)) return GA_EINVAL;
+    run->drop_island = island;
     return GA_OK;
 }
 

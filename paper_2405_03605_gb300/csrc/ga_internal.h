@@ -36,6 +36,12 @@ struct ga_run {
     bool counters_uniform;  // every agent's counter equals `generation` (founder, sync steps)
     int *d_flag;         // device scratch word for ga_load's counter check (workspace header)
     uint2 *d_masks;      // deposit masks of generation sites_base + i (workspace header)
+    // resident stepping (ga_resident.cu): abort word and mailboxes (null when the run is too
+    // large or not synchronous), policy, wait limit and the fault-injection island
+    void *resident_state;
+    uint32_t resident_mode;
+    uint32_t resident_wait_us;
+    uint32_t drop_island;
 };
 
 namespace ga {
@@ -97,6 +103,19 @@ cudaError_t launch_island_async(ga_run *run, const void *src, void *dst, uint32_
                                 uint32_t n_gens, uint32_t first, uint32_t last,
                                 cudaStream_t stream);
 int async_step(ga_run *run, uint32_t n_gens, cudaStream_t stream);
+
+// Resident stepping (ga_resident.cu).  Runs of at most kResidentMaxIslands islands with
+// 16-byte records get the mailbox state in their workspace; GA_RESIDENT_AUTO uses resident
+// launches up to kResidentAutoIslands islands.
+constexpr uint32_t kResidentMaxIslands = 8192;
+constexpr uint32_t kResidentAutoIslands = 8192;
+size_t resident_state_bytes(uint32_t n_islands, uint32_t record_bytes);
+// The run can step resident now: state present, synchronous, counters equal to the generation,
+// a kernel for its island size, and its grid co-resident on the device.
+bool resident_possible(const ga_run *run, uint32_t *blocks);
+// Generations [g0, g0 + n_gens) of the whole run in one cooperative launch (src -> dst).
+cudaError_t launch_resident(ga_run *run, const void *src, void *dst, uint32_t g0, uint32_t n_gens,
+                            cudaStream_t stream);
 
 // Curation sites of ranks [t0, t0 + count); with d_masks (S * bits <= 64) also the deposit
 // masks of those ranks.

@@ -20,6 +20,7 @@ GA_OK = 0
 STEADY, TILTED, HYBRID = 0, 1, 2
 MODEL_TRAIT, MODEL_FITNESS = 0, 1
 SYNC, ASYNC, ASYNC_SEQUENTIAL = 0, 1, 2
+RESIDENT_AUTO, RESIDENT_OFF, RESIDENT_ON = 0, 1, 2
 
 EXPORTED = (
     "ga_config_default", "ga_config_check", "ga_record_bytes", "ga_workspace_bytes",
@@ -29,7 +30,7 @@ EXPORTED = (
     "ga_curation_sites", "ga_mrca_bounds_noalloc", "ga_batch_create", "ga_batch_add",
     "ga_batch_remove", "ga_batch_size", "ga_batch_step", "ga_batch_sync",
     "ga_batch_launch_count", "ga_batch_autotune", "ga_batch_class_warps", "ga_batch_destroy",
-    "ga_async_window", "ga_int_peak",
+    "ga_async_window", "ga_int_peak", "ga_resident_policy", "ga_inject_lost_migrants",
 )
 
 
@@ -100,6 +101,8 @@ def load_library(path=LIB_PATH):
         "ga_batch_destroy": ([vp], C.c_int),
         "ga_async_window": ([vp, u32], C.c_int),
         "ga_int_peak": ([u32, u32, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+        "ga_resident_policy": ([vp, u32, u32], C.c_int),
+        "ga_inject_lost_migrants": ([vp, u32], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -210,6 +213,14 @@ class Run:
     def async_window(self, window):
         """Generations each launch runs in the asynchronous modes (1..256)."""
         _check(self.lib.ga_async_window(self._h, window), "ga_async_window")
+
+    def resident_policy(self, mode, wait_limit_us=1_000_000):
+        """RESIDENT_AUTO / RESIDENT_OFF / RESIDENT_ON and the mailbox wait limit (us)."""
+        _check(self.lib.ga_resident_policy(self._h, mode, wait_limit_us), "ga_resident_policy")
+
+    def inject_lost_migrants(self, island=0xFFFFFFFF):
+        """Fault injection: in resident launches `island` never sends (0xFFFFFFFF: off)."""
+        _check(self.lib.ga_inject_lost_migrants(self._h, island), "ga_inject_lost_migrants")
 
     def step(self, n_gens):
         _check(self.lib.ga_step(self._h, n_gens), "ga_step")

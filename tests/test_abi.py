@@ -73,7 +73,9 @@ def test_async_config_checks(lib):
 
 def test_async_workspace_sizes(lib):
     """16-byte records travel through 16-byte buffers, larger ones through a 16-byte flag
-    word plus the record: four per island, after the two population buffers."""
+    word plus the record: four per island, after the two population buffers.  The synchronous
+    run of 16-byte records carries the resident mailboxes there instead (256 bytes plus two
+    parities of four 16-byte mailboxes per island)."""
     from paper_2405_03605_gb300 import ga
     from paper_2405_03605_gb300.workloads import SMALL_TORUS, ASYNC
     for sites, rb in ((64, 16), (128, 32), (256, 48)):
@@ -81,7 +83,23 @@ def test_async_workspace_sizes(lib):
         extra = ga.workspace_bytes(sync.with_(mode=ASYNC)) - ga.workspace_bytes(sync)
         per_buffer = 16 if rb == 16 else 16 + rb
         want = sync.n_islands * 4 * per_buffer
+        if rb == 16:
+            want -= 256 + sync.n_islands * 128
         assert want <= extra < want + 256, (sites, extra, want)
+
+
+def test_resident_state_sizes(lib):
+    """Resident mailboxes are part of the workspace of synchronous 16-byte-record runs of at
+    most 8,192 islands, and of no other run."""
+    from paper_2405_03605_gb300 import ga
+    from paper_2405_03605_gb300.workloads import SMALL_TORUS
+    def ws(**kw):
+        return ga.workspace_bytes(SMALL_TORUS.with_(**kw))
+    n16 = SMALL_TORUS.with_(rows=64, cols=128)  # 8,192 islands
+    base = ws(rows=64, cols=128, surface_sites=128) - 2 * n16.n_agents * 32
+    assert ws(rows=64, cols=128) - 2 * n16.n_agents * 16 == base + 256 + 8192 * 128
+    over = SMALL_TORUS.with_(rows=64, cols=129)
+    assert ws(rows=64, cols=129) - 2 * over.n_agents * 16 == base
 
 
 def test_sizes(lib):

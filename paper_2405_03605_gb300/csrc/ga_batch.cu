@@ -178,6 +178,9 @@ uint32_t ts_class(uint32_t tsize) { return tsize == 5 ? 5 : 0; }
 // cover.
 constexpr uint32_t kSoloIslands = 1u << 16;
 
+// Side streams a batch uses at most (classes and solo members beyond this share them).
+constexpr size_t kMaxSideStreams = 16;
+
 bool solo(const ga_run *r)
 {
     return r->n_islands >= kSoloIslands || r->cfg.model != GA_MODEL_TRAIT ||
@@ -202,6 +205,12 @@ struct ga_batch {
     bool dirty = true;
     cudaGraphExec_t graph = nullptr;
     uint32_t graph_chunk = 0;
+    // graphs replaced while a launch of them may still be queued: destroyed at the next
+    // host synchronisation of the batch stream
+    std::vector<cudaGraphExec_t> retired;
+    // side streams: class launches and solo members run on these between a fork from and a
+    // join into the batch stream, so independent classes overlap on the GPU
+    std::vector<cudaStream_t> side;
     uint64_t launches = 0;
     int *d_status = nullptr;  // device-check builds: failed index checks of the batch tables
 };
@@ -210,21 +219,75 @@ namespace {
 
 int rc_of(cudaError_t e) { return e == cudaSuccess ? GA_OK : GA_ECUDA; }
 
+// Device tables are allocated and freed in the batch stream's order (cudaMallocAsync /
+// cudaFreeAsync), so a rebuild never waits for the launches already queued: they finish with
+// the tables they were given before those are freed.
 void free_device(ga_batch *b)
 {
     for (auto &c : b->classes) {
-        cudaFree(c.d_unit_run);
-        cudaFree(c.d_unit_local);
+        if (c.d_unit_run) cudaFreeAsync(c.d_unit_run, b->stream);
+        if (c.d_unit_local) cudaFreeAsync(c.d_unit_local, b->stream);
         c.d_unit_run = c.d_unit_local = nullptr;
     }
-    cudaFree(b->d_runs);
-    cudaFree(b->d_sites);
+    if (b->d_runs) cudaFreeAsync(b->d_runs, b->stream);
+    if (b->d_sites) cudaFreeAsync(b->d_sites, b->stream);
     b->d_runs = nullptr;
     b->d_sites = nullptr;
     b->sites_cap = 0;
-    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph) b->retired.push_back(b->graph);
     b->graph = nullptr;
     b->graph_chunk = 0;
+}
+
+// At least `n` side streams (created once, kept until the batch is destroyed).
+int ensure_side(ga_batch *b, size_t n)
+{
+    n = std::min<size_t>(n, ga::kMaxSideStreams);
+    while (b->side.size() < n) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return GA_ECUDA;
+        b->side.push_back(st);
+    }
+    return GA_OK;
+}
+
+// The first `n` side streams wait for the batch stream's work so far (fork), or the batch
+// stream waits for theirs (join); captured as graph dependencies when the batch stream is
+// being captured.
+cudaError_t fork_join(ga_batch *b, size_t n, bool fork)
+{
+    n = std::min(n, b->side.size());
+    for (size_t i = 0; i < n; ++i) {
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        cudaStream_t from = fork ? b->stream : b->side[i], to = fork ? b->side[i] : b->stream;
+        e = cudaEventRecord(ev, from);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+        cudaEventDestroy(ev);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Destroy replaced graphs (the caller has synchronised the batch stream).
+void drop_retired(ga_batch *b)
+{
+    for (cudaGraphExec_t g : b->retired) cudaGraphExecDestroy(g);
+    b->retired.clear();
+}
+
+// Make `waiter` wait, on the device, for the work queued on `from` so far (no host wait).
+cudaError_t order_after(cudaStream_t waiter, cudaStream_t from)
+{
+    if (waiter == from) return cudaSuccess;
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev, from);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(waiter, ev, 0);
+    cudaEventDestroy(ev);
+    return e;
 }
 
 // (Re)build classes, descriptors and block tables after membership or tuning changes.
@@ -290,7 +353,11 @@ int rebuild(ga_batch *b)
         d.pad = 0;
         d.status = r->d_status;
     }
-    if (cudaMalloc(&b->d_runs, n * sizeof(ga::RunDesc)) != cudaSuccess) return GA_ENOMEM;
+    // pageable host sources: each copy is staged before the call returns, so the host vectors
+    // may go out of scope without a wait
+    if (cudaMallocAsync(reinterpret_cast<void **>(&b->d_runs), n * sizeof(ga::RunDesc), b->stream) !=
+        cudaSuccess)
+        return GA_ENOMEM;
     int rc = rc_of(cudaMemcpyAsync(b->d_runs, desc.data(), n * sizeof(ga::RunDesc),
                                    cudaMemcpyHostToDevice, b->stream));
     if (rc != GA_OK) return rc;
@@ -306,8 +373,10 @@ int rebuild(ga_batch *b)
             }
         }
         c.units = static_cast<uint32_t>(ur.size());
-        if (cudaMalloc(&c.d_unit_run, ur.size() * 4) != cudaSuccess ||
-            cudaMalloc(&c.d_unit_local, ul.size() * 4) != cudaSuccess)
+        if (cudaMallocAsync(reinterpret_cast<void **>(&c.d_unit_run), ur.size() * 4, b->stream) !=
+                cudaSuccess ||
+            cudaMallocAsync(reinterpret_cast<void **>(&c.d_unit_local), ul.size() * 4, b->stream) !=
+                cudaSuccess)
             return GA_ENOMEM;
         rc = rc_of(cudaMemcpyAsync(c.d_unit_run, ur.data(), ur.size() * 4, cudaMemcpyHostToDevice,
                                    b->stream));
@@ -316,8 +385,6 @@ int rebuild(ga_batch *b)
                                        cudaMemcpyHostToDevice, b->stream));
         if (rc != GA_OK) return rc;
     }
-    rc = rc_of(cudaStreamSynchronize(b->stream));  // host vectors above go out of scope
-    if (rc != GA_OK) return rc;
     b->expect.clear();
     for (const ga_run *r : b->runs) b->expect.emplace_back(r->generation, r->cur, r->counters_uniform);
     b->dirty = false;
@@ -338,23 +405,31 @@ bool members_moved(const ga_batch *b)
 int ensure_sites(ga_batch *b, uint32_t chunk)
 {
     if (b->sites_cap >= chunk) return GA_OK;
-    cudaFree(b->d_sites);
+    if (b->d_sites) cudaFreeAsync(b->d_sites, b->stream);
     b->d_sites = nullptr;
     const size_t bytes = b->runs.size() * static_cast<size_t>(chunk) * sizeof(int32_t);
-    if (cudaMalloc(&b->d_sites, bytes) != cudaSuccess) return GA_ENOMEM;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&b->d_sites), bytes, b->stream) != cudaSuccess)
+        return GA_ENOMEM;
     b->sites_cap = chunk;
     return GA_OK;
 }
 
 // Enqueue one chunk of `gens` generations for every member run (no host synchronisation).
+// Classes share no run, so each class's launches go to its own side stream between a fork
+// after the site table and a join before the generation advance: the classes' launches of a
+// generation overlap on the GPU.
 int enqueue_chunk(ga_batch *b, uint32_t gens)
 {
     const uint32_t n = static_cast<uint32_t>(b->runs.size());
     ga::batch_sites_kernel<<<std::min<uint32_t>((n * gens + 255) / 256, 4096), 256, 0, b->stream>>>(
         b->d_runs, n, gens, b->d_sites);
     b->launches += 1;
+    if (ensure_side(b, b->classes.size()) != GA_OK) return GA_ECUDA;
+    if (fork_join(b, b->classes.size(), true) != cudaSuccess) return GA_ECUDA;
     for (uint32_t dg = 0; dg < gens; ++dg) {
-        for (const auto &c : b->classes) {
+        for (size_t ci = 0; ci < b->classes.size(); ++ci) {
+            const auto &c = b->classes[ci];
+            cudaStream_t st = b->side[ci % b->side.size()];
             const ga::BatchKernel k =
                 ga::pick(c.island_size, c.sw_class, c.ts_class, c.warps, c.uniform);
             if (!k) return GA_EUNSUPPORTED;
@@ -368,10 +443,11 @@ int enqueue_chunk(ga_batch *b, uint32_t gens)
             a.n_runs = n;
             a.status = b->d_status;
             a.rk = ga::round_keys(ga::Key{static_cast<uint32_t>(c.seed), static_cast<uint32_t>(c.seed >> 32)});
-            k<<<c.units, c.warps * 32, 0, b->stream>>>(a);
+            k<<<c.units, c.warps * 32, 0, st>>>(a);
             b->launches += 1;
         }
     }
+    if (fork_join(b, b->classes.size(), false) != cudaSuccess) return GA_ECUDA;
     ga::batch_advance_kernel<<<(n + 255) / 256, 256, 0, b->stream>>>(b->d_runs, n, gens);
     b->launches += 1;
     return rc_of(cudaGetLastError());
@@ -380,7 +456,7 @@ int enqueue_chunk(ga_batch *b, uint32_t gens)
 int capture_graph(ga_batch *b, uint32_t chunk)
 {
     if (b->graph && b->graph_chunk == chunk) return GA_OK;
-    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph) b->retired.push_back(b->graph);
     b->graph = nullptr;
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -479,9 +555,8 @@ int ga_batch_add(ga_batch *b, ga_run *run)
     if (run->batch) return GA_EINVAL;  // already a member of this or another batch
 
     if (run->generation + 1 > 0xFFFFFFFFull) return GA_EINVAL;
-    // the run's own queued work must be done before the batch stream touches its buffers
-    if (cudaStreamSynchronize(run->stream) != cudaSuccess) return GA_ECUDA;
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return GA_ECUDA;
+    // the run's own queued work comes before anything the batch stream does to its buffers
+    if (order_after(b->stream, run->stream) != cudaSuccess) return GA_ECUDA;
     b->runs.push_back(run);
     run->batch = b;
     b->dirty = true;
@@ -493,8 +568,9 @@ int ga_batch_remove(ga_batch *b, ga_run *run)
     if (!b || !run) return GA_EINVAL;
     auto it = std::find(b->runs.begin(), b->runs.end(), run);
     if (it == b->runs.end()) return GA_EINVAL;
-    // the run leaves the batch even when the wait fails, so that it can still be destroyed
-    const int rc = rc_of(cudaStreamSynchronize(b->stream));
+    // work queued on the run's own stream from now on (and ga_destroy's wait) comes after the
+    // batch's launches that still step it; the run leaves the batch even if that fails
+    const int rc = rc_of(order_after(run->stream, b->stream));
     b->runs.erase(it);
     run->batch = nullptr;
     b->dirty = true;
@@ -517,16 +593,28 @@ int ga_batch_step(ga_batch *b, uint32_t n_gens)
     if (b->dirty || members_moved(b)) {
         // members' own streams may still hold work queued outside the batch
         for (const ga_run *r : b->runs)
-            if (cudaStreamSynchronize(r->stream) != cudaSuccess) return GA_ECUDA;
+            if (order_after(b->stream, r->stream) != cudaSuccess) return GA_ECUDA;
         const int rc = rebuild(b);
         if (rc != GA_OK) return rc;
     }
-    for (ga_run *r : b->runs) {
-        if (!ga::solo(r)) continue;
-        const int rs = ga::step_run(r, n_gens, b->stream);
-        if (rs != GA_OK) return rs;
+    // solo members on side streams of their own (forked from and joined into the batch
+    // stream), overlapping one another and the class launches
+    // (class launches use side streams 0..C-1, solo members the ones after them)
+    size_t n_solo = 0;
+    for (const ga_run *r : b->runs) n_solo += ga::solo(r) ? 1u : 0u;
+    const size_t n_side = b->classes.size() + n_solo;
+    if (n_solo > 0) {
+        if (ensure_side(b, n_side) != GA_OK) return GA_ECUDA;
+        if (fork_join(b, n_side, true) != cudaSuccess) return GA_ECUDA;
+        size_t k = b->classes.size();
+        for (ga_run *r : b->runs) {
+            if (!ga::solo(r)) continue;
+            const int rs = ga::step_run(r, n_gens, b->side[k++ % b->side.size()]);
+            if (rs != GA_OK) return rs;
+        }
     }
     const int rc = step_device(b, n_gens);
+    if (n_solo > 0 && fork_join(b, n_side, false) != cudaSuccess) return GA_ECUDA;
     if (rc != GA_OK) return rc;
     advance_host(b, n_gens);
     return GA_OK;
@@ -536,6 +624,7 @@ int ga_batch_sync(ga_batch *b)
 {
     if (!b) return GA_EINVAL;
     int rc = rc_of(cudaStreamSynchronize(b->stream));
+    if (rc == GA_OK) drop_retired(b);
 #if GA_DEVICE_CHECKS
     // only device-check builds write the batch's status word
     int st = GA_OK;
@@ -635,6 +724,7 @@ int ga_batch_autotune(ga_batch *b, uint32_t trial_gens, uint32_t *chosen_chunk)
     b->chunk = best_chunk;
     if (chosen_chunk) *chosen_chunk = best_chunk;
     cudaStreamSynchronize(b->stream);
+    drop_retired(b);
     for (void *p : saved) cudaFree(p);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -657,6 +747,9 @@ int ga_batch_destroy(ga_batch *b)
     int rc = rc_of(cudaStreamSynchronize(b->stream));
     for (ga_run *r : b->runs) r->batch = nullptr;
     free_device(b);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) rc = GA_ECUDA;
+    drop_retired(b);
+    for (cudaStream_t st : b->side) cudaStreamDestroy(st);
     cudaFree(b->d_status);
     if (b->owns_stream) cudaStreamDestroy(b->stream);
     delete b;

@@ -20,6 +20,7 @@
 //      until it holds a record whose counter is g -- the record is its own ready flag, as
 //      every counter equals the generation -- and place it at the landing slot (the partial
 //      Fisher-Yates draw of the synchronous mode);
+//      meanwhile the island warps compute g's birth draws, which need nothing exchanged;
 //   C. block barrier; island warps land the immigrants and reproduce g and the generations up
 //      to the next migration, while the bookkeeping lanes prepare the next migration
 //      generation's sends (two Philox calls per lane: the neighbour's draw for the emigrant
@@ -208,6 +209,8 @@ resident_kernel(const ResidentArgs a)
     bool aborted = false;
     for (uint32_t it = 0; it < p.n_gens; ++it) {
         const uint32_t g = p.g0 + it;
+        uint4 w[A];
+        bool drawn = false;
         if (g == gm) {  // the same generation for every thread of the block
             __syncthreads();  // A
             uint4 *box = a.mail + static_cast<size_t>((g / a.every_k) & 1u) * p.n_islands * 4u;
@@ -224,6 +227,12 @@ resident_kernel(const ResidentArgs a)
                         }
                     }
                 }
+            }
+            // the generation's birth draws need nothing from the neighbours: the island warps
+            // compute them while the bookkeeping lanes wait for the mailboxes
+            if (valid) {
+                birth_draws<N>(w, p, a.rk, g, island, seg_lane);
+                drawn = true;
             }
             uint4 imm = make_uint4(0u, 0u, 0u, 0u);
             if (bk_ok) {
@@ -297,8 +306,7 @@ resident_kernel(const ResidentArgs a)
             if (gm != ~0u) prepare(gm);
         }
         if (valid) {
-            uint4 w[A];
-            birth_draws<N>(w, p, a.rk, g, island, seg_lane);
+            if (!drawn) birth_draws<N>(w, p, a.rk, g, island, seg_lane);
             reproduce<N, 2, TS, MODEL, 0, 1>(rec, w, p, a.rk, island, seg_lane, mask, g, 0,
                                              gen_mask_at(p, it));
         }
@@ -316,8 +324,11 @@ using ResidentKernel = void (*)(ResidentArgs);
 template <int N, int WARPS>
 ResidentKernel pick_model(uint32_t model, uint32_t tsize)
 {
-    if (model == GA_MODEL_FITNESS)
-        return tsize == 5u ? resident_kernel<N, 5, 1, WARPS> : resident_kernel<N, 0, 1, WARPS>;
+    if (model == GA_MODEL_FITNESS) {  // the float-fitness model: islands of 16 to 64 agents
+        if constexpr (N >= 16 && N <= 64)
+            return tsize == 5u ? resident_kernel<N, 5, 1, WARPS> : resident_kernel<N, 0, 1, WARPS>;
+        return nullptr;
+    }
     return tsize == 5u ? resident_kernel<N, 5, 0, WARPS> : resident_kernel<N, 0, 0, WARPS>;
 }
 

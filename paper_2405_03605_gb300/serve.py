@@ -60,18 +60,49 @@ def _now(t0):
 
 
 def serve_continuous(trace, hbm_budget_bytes, chunk_gens=64, keep_results=False,
-                     autotune=False):
-    """Serve `trace` (list of (arrival_seconds, RunShape)) with continuous batching."""
+                     autotune=False, run_streams=8, max_active_agents=1 << 24):
+    """Serve `trace` (list of (arrival_seconds, RunShape)) with continuous batching.
+
+    The batch advances in chunks of at most `chunk_gens` generations, cut so that runs finish
+    at chunk ends.  Two chunks are kept queued on the batch's stream: while the GPU works on
+    them the host admits arrivals (each new run is created on one of `run_streams` streams;
+    ga_batch_add orders the batch after its founder initialisation without blocking the host)
+    and retires runs whose last chunk has completed, which it learns from a CUDA event.
+
+    Admission is first come first served and stops at the first request that does not fit:
+    in the HBM budget, and in `max_active_agents` agents in flight (about what fills the GPU;
+    a request larger than that is admitted when nothing else runs).  Small requests thus
+    share the GPU while a large one is not slowed by everything admitted beside it."""
+    import collections
     import torch
     stream = torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in range(max(1, run_streams))]
     batch = ga.Batch(stream=stream)
     reqs = [Request(i, t, s) for i, (t, s) in enumerate(trace)]
-    pending = list(reqs)          # in arrival order
-    active = {}                   # rid -> (request, run, remaining generations)
+    pending = collections.deque(reqs)   # in arrival order
+    active = {}                         # rid -> [request, run, remaining generations]
+    inflight = collections.deque()      # (event, [(request, run)] finishing with that chunk)
     used = 0
     peak = 0
+    agents = 0  # agents of the admitted, unfinished runs
+    created = 0
+    tuned = not autotune
     t0 = time.perf_counter()
-    while pending or active:
+
+    def retire_oldest():
+        nonlocal used, agents
+        ev, finishing = inflight.popleft()
+        ev.synchronize()
+        now = _now(t0)
+        for req, run in finishing:
+            req.finished = now
+            if keep_results:
+                req.result = run.snapshot()
+            used -= ga.workspace_bytes(req.shape)
+            agents -= req.shape.n_agents
+            run.close()
+
+    while pending or active or inflight:
         now = _now(t0)
         # admission: arrived requests, first come first served, while they fit
         while pending and pending[0].arrival <= now:
@@ -80,37 +111,44 @@ def serve_continuous(trace, hbm_budget_bytes, chunk_gens=64, keep_results=False,
                 raise ValueError(f"request {pending[0].rid} alone exceeds the HBM budget")
             if used + need > hbm_budget_bytes:
                 break
-            req = pending.pop(0)
-            run = ga.Run(req.shape, stream=stream)
+            if agents > 0 and agents + pending[0].shape.n_agents > max_active_agents:
+                break
+            req = pending.popleft()
+            run = ga.Run(req.shape, stream=streams[created % len(streams)])
+            created += 1
             batch.add(run)
             req.admitted = _now(t0)
             active[req.rid] = [req, run, req.shape.generations]
             used += need
+            agents += req.shape.n_agents
             peak = max(peak, used)
-        if not active:
-            if pending:
-                time.sleep(max(0.0, min(pending[0].arrival - _now(t0), 0.01)))
-            continue
-        if autotune:
-            batch.autotune(trial_gens=4)
-            autotune = False
-        step = min(chunk_gens, min(a[2] for a in active.values()))
-        batch.step(step)
-        batch.sync()
-        done = []
-        for rid, a in active.items():
-            a[2] -= step
-            if a[2] == 0:
-                done.append(rid)
-        for rid in done:
-            req, run, _ = active.pop(rid)
-            batch.remove(run)
-            req.finished = _now(t0)
-            if keep_results:
-                req.result = run.snapshot()
-            used -= ga.workspace_bytes(req.shape)
-            run.close()
+        if active:
+            if not tuned:
+                batch.autotune(trial_gens=4)
+                tuned = True
+            step = min(chunk_gens, min(a[2] for a in active.values()))
+            batch.step(step)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            finishing = []
+            for rid in list(active):
+                a = active[rid]
+                a[2] -= step
+                if a[2] == 0:
+                    finishing.append((a[0], a[1]))
+                    batch.remove(a[1])
+                    del active[rid]
+            inflight.append((ev, finishing))
+        # keep at most two chunks queued (with nothing left to launch, wait for the oldest),
+        # and retire every run whose last chunk has completed
+        while inflight and (len(inflight) > 2 or not active):
+            retire_oldest()
+        while inflight and inflight[0][0].query():
+            retire_oldest()
+        if not active and not inflight and pending:
+            time.sleep(max(0.0, min(pending[0].arrival - _now(t0), 0.01)))
     makespan = _now(t0)
+    batch.sync()
     launches = batch.launches
     batch.close()
     return ServeReport(reqs, makespan, float(sum(r.work for r in reqs)), launches, peak)

@@ -46,21 +46,19 @@ struct RunDesc {
 struct BatchArgs {
     const RunDesc *__restrict__ runs;
     const uint32_t *__restrict__ unit_run;    // block -> run index
-    const uint32_t *__restrict__ unit_local;  // block -> unit within the run
+    const uint32_t *__restrict__ unit_local;  // block -> unit (or chunk of units) within the run
     const int32_t *__restrict__ sites;        // [run][chunk] curation sites of the chunk
+    const uint2 *__restrict__ masks;          // [run][chunk] deposit masks (64-bit surfaces)
     uint32_t chunk, dg;                       // chunk length, generation within the chunk
     uint32_t n_runs;
     int *status;                              // the batch's device status word
     RoundKeys rk;
 };
 
-template <int N, int SW, int TS, int W, int CF = 1>
-__global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
+// The block's run parameters, staged once in shared memory by thread 0: the block body reads
+// them from there (uniform, broadcast) instead of holding them in registers.
+__device__ __forceinline__ void stage_params(const BatchArgs &a, RunParams &s_r, uint32_t &s_unit)
 {
-    // the block's run parameters, staged once in shared memory: the block body reads them
-    // from there (uniform, broadcast) instead of holding them in registers
-    __shared__ RunParams s_r;
-    __shared__ uint32_t s_unit;
     if (threadIdx.x == 0) {
         uint32_t run = __ldg(&a.unit_run[blockIdx.x]);
         if (!in_bounds(run < a.n_runs, a.status)) run = 0;
@@ -88,20 +86,50 @@ __global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
         s_r.effect_scale = 1.0f;
         s_r.gen_sites_left = a.chunk - a.dg;
         s_r.status = d.status;
+        s_r.gen_masks = a.masks + static_cast<size_t>(run) * a.chunk + a.dg;
+        s_r.dif_mask = (1u << d.bits) - 1u;
+        s_r.dif_rep = d.bits == 1u ? 0xFFFFFFFFu : d.bits == 2u ? 0x55555555u
+                    : d.bits == 4u ? 0x11111111u : 0x01010101u;
         s_unit = __ldg(&a.unit_local[blockIdx.x]);
     }
     __syncthreads();
+}
+
+template <int N, int SW, int TS, int W, int CF = 1>
+__global__ void __launch_bounds__(W * 32) batch_step_kernel(const BatchArgs a)
+{
+    __shared__ RunParams s_r;
+    __shared__ uint32_t s_unit;
+    stage_params(a, s_r, s_unit);
     step_block<N, SW, TS, W, 0, CF>(s_r, a.rk, s_unit);
 }
 
+// Classes of 16-byte records whose counters all equal their generation, islands of 16, 32 or
+// 64 agents: the multi-unit block body of the single-run kernel (step_units); a block runs a
+// chunk of units_per_block<N>() units of one member.
+template <int N, int TS>
+__global__ void __launch_bounds__(256, (N >= 64 ? 6 : 8)) batch_units_kernel(const BatchArgs a)
+{
+    __shared__ RunParams s_r;
+    __shared__ uint32_t s_unit;
+    stage_params(a, s_r, s_unit);
+    step_units<N, TS, units_per_block<N>()>(s_r, a.rk, s_unit);
+}
+
 __global__ void batch_sites_kernel(const RunDesc *__restrict__ runs, uint32_t n_runs,
-                                   uint32_t chunk, int32_t *__restrict__ sites)
+                                   uint32_t chunk, int32_t *__restrict__ sites,
+                                   uint2 *__restrict__ masks)
 {
     const uint32_t total = n_runs * chunk;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += gridDim.x * blockDim.x) {
         const RunDesc &d = runs[i / chunk];
-        sites[i] = curation_site(d.policy, d.log2_sites, d.sites, d.g + i % chunk);
+        const int site = curation_site(d.policy, d.log2_sites, d.sites, d.g + i % chunk);
+        sites[i] = site;
+        // deposit masks within surface words 0 and 1 (used by members with 64-bit surfaces)
+        const uint32_t pos = site >= 0 ? static_cast<uint32_t>(site) * d.bits : 0u;
+        const uint32_t m = (site >= 0 && pos < 64u) ? ((1u << d.bits) - 1u) << (pos & 31u) : 0u;
+        masks[i] = make_uint2(pos < 32u ? m : 0u, pos < 32u ? 0u : m);
     }
 }
 
@@ -139,6 +167,10 @@ BatchKernel pick_ts(uint32_t ts, uint32_t warps)
 template <int N>
 BatchKernel pick_sw(uint32_t sw, uint32_t ts, uint32_t warps, bool uniform)
 {
+    if constexpr (N >= 16 && N <= 64) {
+        if (sw <= 2 && uniform)
+            return ts == 5 ? batch_units_kernel<N, 5> : batch_units_kernel<N, 0>;
+    }
     if (sw <= 2) return uniform ? pick_ts<N, 2, 0>(ts, warps) : pick_ts<N, 2, 1>(ts, warps);
     if (sw <= 6) return pick_ts<N, 6, 1>(ts, warps);
     if (sw <= 8) return pick_ts<N, 8, 1>(ts, warps);
@@ -164,6 +196,25 @@ struct Class {
     uint64_t seed;
     bool uniform = false;  // every member's counters equal its generation (no closed form)
     uint32_t warps = 8;
+    // islands one block covers: warps x islands per warp, or for the multi-unit kernel of
+    // uniform 16-byte classes (8 warps, fixed) its units per block x islands per unit
+    uint32_t per_block() const
+    {
+        const uint32_t per_warp = island_size >= 32 ? 1u : 32u / island_size;
+        if (uniform && sw_class == 2u && island_size >= 16u && island_size <= 64u) {
+            const uint32_t units = island_size == 16u ? static_cast<uint32_t>(units_per_block<16>())
+                                 : island_size == 32u ? static_cast<uint32_t>(units_per_block<32>())
+                                                      : static_cast<uint32_t>(units_per_block<64>());
+            return units * 8u * per_warp;
+        }
+        return warps * per_warp;
+    }
+    // threads per block of the class's kernel
+    uint32_t threads() const
+    {
+        return (uniform && sw_class == 2u && island_size >= 16u && island_size <= 64u) ? 256u
+                                                                                       : warps * 32u;
+    }
     std::vector<uint32_t> members;  // indices into the batch's run list
     uint32_t *d_unit_run = nullptr, *d_unit_local = nullptr;
     uint32_t units = 0;
@@ -200,6 +251,7 @@ struct ga_batch {
     std::vector<ga::Class> classes;
     ga::RunDesc *d_runs = nullptr;
     int32_t *d_sites = nullptr;
+    uint2 *d_masks = nullptr;  // deposit masks, laid out as d_sites
     uint32_t sites_cap = 0;  // chunk length the site table holds
     uint32_t chunk = 64;
     bool dirty = true;
@@ -231,8 +283,10 @@ void free_device(ga_batch *b)
     }
     if (b->d_runs) cudaFreeAsync(b->d_runs, b->stream);
     if (b->d_sites) cudaFreeAsync(b->d_sites, b->stream);
+    if (b->d_masks) cudaFreeAsync(b->d_masks, b->stream);
     b->d_runs = nullptr;
     b->d_sites = nullptr;
+    b->d_masks = nullptr;
     b->sites_cap = 0;
     if (b->graph) b->retired.push_back(b->graph);
     b->graph = nullptr;
@@ -362,8 +416,7 @@ int rebuild(ga_batch *b)
                                    cudaMemcpyHostToDevice, b->stream));
     if (rc != GA_OK) return rc;
     for (auto &c : b->classes) {
-        const uint32_t per_warp = c.island_size >= 32 ? 1u : 32u / c.island_size;
-        const uint32_t per_block = c.warps * per_warp;
+        const uint32_t per_block = c.per_block();
         std::vector<uint32_t> ur, ul;
         for (uint32_t m : c.members) {
             const uint32_t units = (b->runs[m]->n_islands + per_block - 1) / per_block;
@@ -406,9 +459,14 @@ int ensure_sites(ga_batch *b, uint32_t chunk)
 {
     if (b->sites_cap >= chunk) return GA_OK;
     if (b->d_sites) cudaFreeAsync(b->d_sites, b->stream);
+    if (b->d_masks) cudaFreeAsync(b->d_masks, b->stream);
     b->d_sites = nullptr;
-    const size_t bytes = b->runs.size() * static_cast<size_t>(chunk) * sizeof(int32_t);
-    if (cudaMallocAsync(reinterpret_cast<void **>(&b->d_sites), bytes, b->stream) != cudaSuccess)
+    b->d_masks = nullptr;
+    const size_t entries = b->runs.size() * static_cast<size_t>(chunk);
+    if (cudaMallocAsync(reinterpret_cast<void **>(&b->d_sites), entries * sizeof(int32_t), b->stream) !=
+            cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void **>(&b->d_masks), entries * sizeof(uint2), b->stream) !=
+            cudaSuccess)
         return GA_ENOMEM;
     b->sites_cap = chunk;
     return GA_OK;
@@ -422,7 +480,7 @@ int enqueue_chunk(ga_batch *b, uint32_t gens)
 {
     const uint32_t n = static_cast<uint32_t>(b->runs.size());
     ga::batch_sites_kernel<<<std::min<uint32_t>((n * gens + 255) / 256, 4096), 256, 0, b->stream>>>(
-        b->d_runs, n, gens, b->d_sites);
+        b->d_runs, n, gens, b->d_sites, b->d_masks);
     b->launches += 1;
     if (ensure_side(b, b->classes.size()) != GA_OK) return GA_ECUDA;
     if (fork_join(b, b->classes.size(), true) != cudaSuccess) return GA_ECUDA;
@@ -438,12 +496,13 @@ int enqueue_chunk(ga_batch *b, uint32_t gens)
             a.unit_run = c.d_unit_run;
             a.unit_local = c.d_unit_local;
             a.sites = b->d_sites;
+            a.masks = b->d_masks;
             a.chunk = gens;
             a.dg = dg;
             a.n_runs = n;
             a.status = b->d_status;
             a.rk = ga::round_keys(ga::Key{static_cast<uint32_t>(c.seed), static_cast<uint32_t>(c.seed >> 32)});
-            k<<<c.units, c.warps * 32, 0, st>>>(a);
+            k<<<c.units, c.threads(), 0, st>>>(a);
             b->launches += 1;
         }
     }

@@ -436,17 +436,19 @@ __device__ __forceinline__ void step_block(const RunParams &p, const RoundKeys &
 }
 
 // ---------------------------------------------------------------------------------------
-// Multi-unit blocks for 32-agent islands with 16-byte records whose counters all equal the
-// generation (the paper-scale workload).  A block of 8 warps runs U units of 8 islands in
-// turn; warp w runs island w of every unit.  Each island's records come into shared memory by
-// asynchronous copies (cp.async): the next unit's while the current one is computed, so a
-// warp never waits for a record load except the block's first.  The migration bookkeeping of
-// all U units is done once, at the start, by warps 0..U-1 (warp u: unit u, one lane per
-// (island, direction), as in step_block), so it is spread over the block's warps instead of
-// all falling to warp 0, and its immigrant copies go straight into shared memory.  An
-// island's lanes then find their landing direction in a per-island table of 32 bytes (0xFF:
-// no immigrant) and take the immigrant record from shared memory.  Deposits use the
-// generation's precomputed masks.  The only block barrier is the one after the bookkeeping.
+// Multi-unit blocks for islands of 16, 32 or 64 agents with 16-byte records whose counters
+// all equal the generation (every synchronous run unless a population with other counters
+// was loaded).  A block of 8 warps runs U units of 8 * P islands in turn (P = 32 / N islands
+// per warp below 32 agents, one island per warp otherwise); warp w runs its share of every
+// unit.  Each warp's records come into shared memory by asynchronous copies (cp.async): the
+// next unit's while the current one is computed, so a warp never waits for a record load
+// except the block's first.  The migration bookkeeping of all U units is done once, at the
+// start, spread over the block's threads (unit u: threads [u * 4BI, (u + 1) * 4BI), one per
+// (island, direction), as in step_block), and its immigrant copies go straight into shared
+// memory.  An island's lanes then find their landing direction in a per-island table of N
+// bytes (0xFF: no immigrant) and take the immigrant record from shared memory.  Deposits use
+// the generation's precomputed masks.  The only block barrier is the one after the
+// bookkeeping.
 // ---------------------------------------------------------------------------------------
 
 // 16-byte asynchronous global -> shared copy (bypassing L1), and its group operations.
@@ -459,40 +461,60 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int PENDING>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" :: "n"(PENDING) : "memory"); }
 
-template <int TS, int U>
+// Units per block: as many as the block's 256 threads can do the bookkeeping for, at most 8.
+template <int N>
+constexpr int units_per_block()
+{
+    return (256 / (4 * 8 * Shape<N>::P)) < 8 ? (256 / (4 * 8 * Shape<N>::P)) : 8;
+}
+
+template <int N, int TS, int U, int MODEL = 0>
 __device__ __forceinline__ void step_units(const RunParams &p, const RoundKeys &rk, uint32_t blk)
 {
-    constexpr int N = 32, SW = 2, LW = 4, WARPS = 8;
-    static_assert(U >= 1 && U <= WARPS, "warp u does the bookkeeping of unit u");
-    __shared__ uint4 s_rec[WARPS][2][32];        // per warp: current and next island's records
-    __shared__ uint4 s_imm[U][WARPS * 4];        // immigrants by (unit, island, direction)
-    __shared__ __align__(16) uint8_t s_dir[U][WARPS][32];  // landing direction of each slot
+    constexpr int SW = 2, LW = 4, WARPS = 8;
+    constexpr int A = Shape<N>::A, P = Shape<N>::P, SEG = Shape<N>::SEG;
+    constexpr int BI = WARPS * P;  // islands per unit
+    constexpr int ML = 4 * BI;     // bookkeeping lanes per unit (a multiple of 32)
+    constexpr int RPW = 32 * A;    // records per warp and unit
+    static_assert(N >= 16 && N <= 64, "islands of 16 to 64 agents");
+    static_assert(U >= 1 && U * ML <= WARPS * 32, "the block's threads cover every unit's bookkeeping");
+    __shared__ uint4 s_rec[WARPS][2][RPW];                   // per warp: current and next unit's records
+    __shared__ uint4 s_imm[U][ML];                           // immigrants by (unit, island, direction)
+    __shared__ __align__(16) uint8_t s_dir[U][BI][N];        // landing direction of each slot
 
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t warp = threadIdx.x >> 5;
-    const uint32_t island0 = blk * (U * WARPS);  // first island of the block's first unit
+    const uint32_t seg_lane = lane % SEG;
+    const uint32_t local = warp * P + lane / SEG;  // this lane's island within a unit
+    const uint32_t island0 = blk * (U * BI);       // first island of the block's first unit
 
-    // the first unit's records
+    // the first unit's records: the warp's P islands are 32 A consecutive records
     {
-        const uint32_t island = island0 + warp;
-        if (island < p.n_islands) cp_async16(&s_rec[warp][0][lane], &p.src[static_cast<size_t>(island) * N + lane]);
+        const uint32_t island = island0 + local;
+        if (island < p.n_islands) {
+            const uint4 *src = p.src + static_cast<size_t>(island0 + warp * P) * N + lane;
+#pragma unroll
+            for (int ag = 0; ag < A; ++ag) cp_async16(&s_rec[warp][0][lane + 32u * ag], src + 32u * ag);
+        }
         cp_async_commit();
     }
 
-    // migration bookkeeping of unit `warp`: lane (island i, direction d); the birth draw of
+    // migration bookkeeping of unit t / ML: lane (island i, direction d); the birth draw of
     // slot d carries the immigrant index (bits 8..15) and the landing draw (bits 16..31)
-    if (p.migrate && warp < static_cast<uint32_t>(U)) {
-        uint32_t *dirw = reinterpret_cast<uint32_t *>(&s_dir[warp][0][0]);
-        dirw[lane] = 0xFFFFFFFFu;
-        dirw[lane + 32u] = 0xFFFFFFFFu;
-        const uint32_t li = lane >> 2, md = lane & 3u;
-        const uint32_t isl = island0 + warp * WARPS + li;
+    if (p.migrate && threadIdx.x < static_cast<uint32_t>(U * ML)) {
+        const uint32_t u = threadIdx.x / ML, idx = threadIdx.x % ML;
+        const uint32_t li = idx >> 2, md = idx & 3u;
+        // the island's own four lanes clear its table (N bytes)
+        uint32_t *dirw = reinterpret_cast<uint32_t *>(&s_dir[u][li][0]);
+#pragma unroll
+        for (uint32_t k = md; k < static_cast<uint32_t>(N / 4); k += 4u) dirw[k] = 0xFFFFFFFFu;
+        const uint32_t isl = island0 + u * BI + li;
         const bool ok = isl < p.n_islands;
         uint32_t r = md;
         if (ok) {
-            const uint32_t u = philox_rk(p.g0, isl, md | (kBirth << 16), p.run_id, rk).w;
-            r = md + (((u >> 16) * static_cast<uint32_t>(N - md)) >> 16);
-            const uint32_t e = (((u >> 8) & 0xFFu) * N) >> 8;
+            const uint32_t w3 = philox_rk(p.g0, isl, md | (kBirth << 16), p.run_id, rk).w;
+            r = md + (((w3 >> 16) * static_cast<uint32_t>(N - md)) >> 16);
+            const uint32_t e = (((w3 >> 8) & 0xFFu) * N) >> 8;
             const uint32_t y = div_cols(isl, p.cols_m, p.cols_l), x = isl - y * p.cols;
             const uint32_t yn = md == 0u ? (y == 0u ? p.rows - 1u : y - 1u)
                               : md == 1u ? (y + 1u == p.rows ? 0u : y + 1u) : y;
@@ -500,7 +522,7 @@ __device__ __forceinline__ void step_units(const RunParams &p, const RoundKeys &
                               : md == 3u ? (x == 0u ? p.cols - 1u : x - 1u) : x;
             const uint32_t nb = yn * p.cols + xn;
             if (in_bounds(nb < p.n_islands, p.status))
-                cp_async16(&s_imm[warp][lane], &p.src[static_cast<size_t>(nb) * N + e]);
+                cp_async16(&s_imm[u][idx], &p.src[static_cast<size_t>(nb) * N + e]);
         }
         cp_async_commit();
         // partial Fisher-Yates over [0, N) in direction order among the island's four lanes
@@ -519,8 +541,9 @@ __device__ __forceinline__ void step_units(const RunParams &p, const RoundKeys &
             if (static_cast<uint32_t>(dd) == md) slot = vr;
             v[dd] = vd;
         }
-        __syncwarp();  // the table is cleared before any entry is set
-        if (ok) s_dir[warp][li][slot & 31u] = static_cast<uint8_t>(md);
+        __syncwarp();  // the table is cleared before any entry is set (same warp)
+        if (ok && in_bounds(slot < static_cast<uint32_t>(N), p.status))
+            s_dir[u][li][slot] = static_cast<uint8_t>(md);
         cp_async_wait<0>();
     }
     __syncthreads();
@@ -528,29 +551,52 @@ __device__ __forceinline__ void step_units(const RunParams &p, const RoundKeys &
     const uint2 dmask = gen_mask_at(p, 0u);
 #pragma unroll 1
     for (uint32_t un = 0; un < static_cast<uint32_t>(U); ++un) {
-        const uint32_t island = island0 + un * WARPS + warp;
-        if (island >= p.n_islands) break;  // uniform in the warp; later units lie further on
-        const uint32_t nxt = island + WARPS;
-        if (un + 1u < static_cast<uint32_t>(U) && nxt < p.n_islands)
-            cp_async16(&s_rec[warp][(un + 1u) & 1u][lane], &p.src[static_cast<size_t>(nxt) * N + lane]);
+        const uint32_t first = island0 + un * BI + warp * P;  // the warp's first island
+        if (first >= p.n_islands) break;  // uniform in the warp; later units lie further on
+        const uint32_t island = first + lane / SEG;
+        bool valid = true;  // one island per warp: the whole warp, checked above
+        unsigned mask = 0xffffffffu;
+        if constexpr (P > 1) {
+            valid = island < p.n_islands;
+            mask = __ballot_sync(0xffffffffu, valid);
+        }
+        if (un + 1u < static_cast<uint32_t>(U) && island + BI < p.n_islands) {
+            const uint4 *src = p.src + static_cast<size_t>(first + BI) * N + lane;
+#pragma unroll
+            for (int ag = 0; ag < A; ++ag)
+                cp_async16(&s_rec[warp][(un + 1u) & 1u][lane + 32u * ag], src + 32u * ag);
+        }
         cp_async_commit();
-        uint4 w[1];
-        birth_draws<N>(w, p, rk, p.g0, island, lane);
-        cp_async_wait<1>();  // this island's records have landed
-        uint4 v = s_rec[warp][un & 1u][lane];
-        if (p.migrate) {
-            const uint32_t dd = s_dir[un][warp][lane];
-            const uint4 x = s_imm[un][warp * 4u + (dd & 3u)];
-            if (dd < 4u) v = x;
+        if constexpr (P > 1) {
+            if (!valid) break;  // only lanes of a missing last island; later units are past too
         }
-        uint32_t rec[1][LW] = {{v.x, v.y, v.z, v.w}};
-        reproduce<N, SW, TS, 0, 0, 1>(rec, w, p, rk, island, lane, 0xffffffffu, p.g0, 0, dmask);
+        uint4 w[A];
+        birth_draws<N>(w, p, rk, p.g0, island, seg_lane);
+        cp_async_wait<1>();  // this unit's records have landed
+        uint32_t rec[A][LW];
+#pragma unroll
+        for (int ag = 0; ag < A; ++ag) {
+            uint4 v = s_rec[warp][un & 1u][lane + 32u * ag];
+            if (p.migrate) {
+                const uint32_t dd = s_dir[un][local][seg_lane + 32u * ag];
+                const uint4 x = s_imm[un][local * 4u + (dd & 3u)];
+                if (dd < 4u) v = x;
+            }
+            rec[ag][0] = v.x;
+            rec[ag][1] = v.y;
+            rec[ag][2] = v.z;
+            rec[ag][3] = v.w;
+        }
+        reproduce<N, SW, TS, MODEL, 0, 1>(rec, w, p, rk, island, seg_lane, mask, p.g0, 0, dmask);
         for (uint32_t it = 1; it < p.n_gens; ++it) {
-            birth_draws<N>(w, p, rk, p.g0 + it, island, lane);
-            reproduce<N, SW, TS, 0, 0, 1>(rec, w, p, rk, island, lane, 0xffffffffu, p.g0 + it, 0,
-                                          gen_mask_at(p, it));
+            birth_draws<N>(w, p, rk, p.g0 + it, island, seg_lane);
+            reproduce<N, SW, TS, MODEL, 0, 1>(rec, w, p, rk, island, seg_lane, mask, p.g0 + it, 0,
+                                              gen_mask_at(p, it));
         }
-        p.dst[static_cast<size_t>(island) * N + lane] = make_uint4(rec[0][0], rec[0][1], rec[0][2], rec[0][3]);
+        uint4 *dst = p.dst + static_cast<size_t>(first) * N + lane;
+#pragma unroll
+        for (int ag = 0; ag < A; ++ag)
+            dst[32u * ag] = make_uint4(rec[ag][0], rec[ag][1], rec[ag][2], rec[ag][3]);
     }
 }
 

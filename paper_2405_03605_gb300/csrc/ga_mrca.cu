@@ -175,11 +175,14 @@ cudaError_t launch_rank_table(uint32_t *order, uint32_t *ranks, uint32_t *meta, 
 // One warp per sampled agent: lanes 0..7 hold the agent's surface words; for packed word w,
 // lane l gathers differentia index w * (32/b) + l (site order[i], fetched from the lane that
 // holds its surface word) and one warp OR-reduction assembles the word.
+// reverse64 (strings of at most 64 bits): the 64-bit string (word 1 : word 0) is stored
+// bit-reversed, so the first rank index sits at bit 63 and a pair's first mismatch is the
+// count of leading zeros of the XOR.
 __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_words,
                             uint32_t n_agents, const uint32_t *__restrict__ ids, uint32_t n,
                             const uint32_t *__restrict__ order, const uint32_t *__restrict__ meta,
                             uint32_t bits, uint32_t T, uint32_t *__restrict__ packed,
-                            int *__restrict__ status)
+                            int *__restrict__ status, uint32_t reverse64)
 {
     __shared__ uint32_t ord[256];
     release_next_grid();  // the pair kernel may start its index set-up
@@ -212,6 +215,10 @@ __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_wo
             if (lane == w) word_out = full;
         }
     }
+    if (reverse64) {  // lanes 0 and 1 swap words and reverse their bits
+        const uint32_t other = __shfl_xor_sync(0xffffffffu, word_out, 1);
+        if (lane < 2u) word_out = __brev(other);
+    }
     if (lane < kPackWords) packed[static_cast<size_t>(a) * kPackWords + lane] = word_out;
 }
 
@@ -225,11 +232,12 @@ __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_wo
 // pairs).  The first set bit of packed[i] ^ packed[j] gives the first mismatching rank index
 // i*.  With 0-based sorted ranks r_0 < ... < r_{m-1}, a mismatch at index i* gives
 // hi = r_{i*}, lo = r_{i*-K} + 1 (0 if i* < K), and no mismatch hi = T, lo = r_{m-K} + 1.
-// 64-bit strings (S*b <= 64): the bits past m*b are zero in every string, so "no mismatch"
-// reads as i* = m, and one shared table holds both bounds for every i* in [0, m]:
-// tab[r] = (r >= K ? r_{r-K} + 1 : 0, r < m ? r_r : T).  WIDE strings (more than 64 bits)
-// take the first nonzero word of the XOR and the two rules separately (measured faster for
-// them than the table).
+// 64-bit strings (S*b <= 64) are stored bit-reversed (pack_kernel): a pair's first mismatching
+// bit is the count c of leading zeros of the XOR, 64 when none (the bits past m*b are zero in
+// every string), and one shared table holds both bounds for every c in [0, 64]:
+// i* = min(c / b, m), tab[c] = (i* >= K ? r_{i*-K} + 1 : 0, i* < m ? r_{i*} : T).  WIDE
+// strings (more than 64 bits) take the first nonzero word of the XOR and the two rules
+// separately (measured faster for them than a table).
 template <bool WIDE>
 __global__ void __launch_bounds__(kPairThreads)
 pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__restrict__ ranks_g,
@@ -237,7 +245,7 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
             uint32_t per_warp, uint32_t *__restrict__ lo, uint32_t *__restrict__ hi,
             int *__restrict__ status)
 {
-    __shared__ uint2 tab[WIDE ? 1 : 257];
+    __shared__ uint2 tab[WIDE ? 1 : 65];
     __shared__ uint32_t ranks[WIDE ? 256 : 1];
     // pairs [warp * per_warp, (warp + 1) * per_warp) of n (n - 1) / 2 (per_warp: a multiple of
     // 32 chosen on the host so that the grid covers every pair)
@@ -265,8 +273,11 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
     wait_previous_grid();
     const uint32_t m = meta[0];
     if constexpr (!WIDE) {
-        for (uint32_t r = threadIdx.x; r <= m; r += blockDim.x)
-            tab[r] = make_uint2(r >= K ? ranks_g[r - K] + 1u : 0u, r < m ? ranks_g[r] : T);
+        for (uint32_t c = threadIdx.x; c <= 64u; c += blockDim.x) {
+            uint32_t r = c >> log2_bits;
+            r = r < m ? r : m;
+            tab[c] = make_uint2(r >= K ? ranks_g[r - K] + 1u : 0u, r < m ? ranks_g[r] : T);
+        }
     } else {
         for (uint32_t r = threadIdx.x; r < m; r += blockDim.x) ranks[r] = ranks_g[r];
     }
@@ -290,11 +301,7 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
         if constexpr (!WIDE) {
             const unsigned long long x =
                 __ldg(reinterpret_cast<const unsigned long long *>(packed) + j * (kPackWords / 2u)) ^ a0n;
-            // first differing bit, 64 if none
-            const uint32_t first_bit = static_cast<uint32_t>(__clzll(static_cast<long long>(__brevll(x))));
-            uint32_t istar = first_bit >> log2_bits;
-            istar = istar < m ? istar : m;
-            const uint2 bound = tab[istar];
+            const uint2 bound = tab[__clzll(static_cast<long long>(x))];  // first differing bit, 64: none
             __stcs(lo_q, bound.x);
             __stcs(hi_q, bound.y);
         } else {
@@ -340,9 +347,11 @@ cudaError_t launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, ui
                            uint32_t bits, uint32_t K, uint32_t T, uint32_t *packed,
                            uint32_t *d_lo, uint32_t *d_hi, int *status, cudaStream_t stream)
 {
+    // sites * bits <= 64: every rank-ordered string fits in its first 64 bits (bit-reversed)
+    const bool narrow = sites * bits <= 64u;
     const cudaError_t e = launch_dependent(pack_kernel, (n + 7u) / 8u, 256, stream, pop,
                                            record_words, n_agents, d_ids, n, order, meta, bits, T,
-                                           packed, status);
+                                           packed, status, narrow ? 1u : 0u);
     if (e != cudaSuccess) return e;
     // enough resident blocks for the whole GPU, each thread then sweeping several pairs
     const unsigned long long pairs = static_cast<unsigned long long>(n) * (n - 1u) / 2ull;
@@ -352,8 +361,7 @@ cudaError_t launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, ui
     const uint32_t per_warp =
         static_cast<uint32_t>(((pairs + n_warps - 1ull) / n_warps + 31ull) / 32ull * 32ull);
     const uint32_t log2_bits = bits == 1u ? 0u : bits == 2u ? 1u : bits == 4u ? 2u : 3u;
-    // sites * bits <= 64: every rank-ordered string fits in its first 64 bits
-    return launch_dependent(sites * bits <= 64u ? pair_kernel<false> : pair_kernel<true>, grid,
+    return launch_dependent(narrow ? pair_kernel<false> : pair_kernel<true>, grid,
                             kPairThreads, stream, packed, n, ranks, meta, log2_bits, K, T, per_warp,
                             d_lo, d_hi, status);
 }

@@ -21,17 +21,18 @@ __global__ void __launch_bounds__(kStepThreads) island_step_kernel(const StepArg
     step_block<N, SW, TS, kStepWarps, MODEL, CF>(a.r, a.rk, blockIdx.x);
 }
 
-// Units of 8 islands run by one block of the multi-unit kernel (32-agent islands, 16-byte
-// records, counters equal to the generation; step_units in ga_island.cuh).  0: not used.
-#ifndef GA_UNITS_PER_BLOCK
-#define GA_UNITS_PER_BLOCK 8
-#endif
-constexpr int kUnits = GA_UNITS_PER_BLOCK;
+// Multi-unit kernel (step_units in ga_island.cuh) for 16-byte records whose counters all
+// equal the generation, islands of 16, 32 or 64 agents, any tournament size, both genome
+// models; TS = 0 reads the tournament size from the run.
+// Resident blocks per SM asked of the compiler: 8 (32 registers) below 64 agents; the two
+// agents per lane of 64-agent islands need 40 registers (6 blocks).
+template <int N>
+constexpr int units_min_blocks() { return N >= 64 ? 6 : 8; }
 
-template <int TS, int U>
-__global__ void __launch_bounds__(kStepThreads, 8) island_units_kernel(const StepArgs a)
+template <int N, int TS, int MODEL>
+__global__ void __launch_bounds__(kStepThreads, units_min_blocks<N>()) island_units_kernel(const StepArgs a)
 {
-    step_units<TS, U>(a.r, a.rk, blockIdx.x);
+    step_units<N, TS, units_per_block<N>(), MODEL>(a.r, a.rk, blockIdx.x);
 }
 
 // Every record becomes the founder: trait 0, counter 0, surface word w = word 0 of
@@ -265,17 +266,39 @@ cudaError_t launch_island_step(ga_run *run, const void *src, void *dst, uint32_t
 {
     const bool uniform = run->cfg.mode == GA_SYNC && run->counters_uniform &&
                          run->cfg.tournament_size == 5;
-    if (kUnits > 0 && uniform && run->cfg.island_size == 32 && run->surface_words <= 2 &&
-        run->cfg.model == GA_MODEL_TRAIT) {
-        StepArgs a;
-        a.r = run_params(run, src, dst, g0, n_gens, migrate);
-        a.rk = round_keys(Key{static_cast<uint32_t>(run->cfg.seed),
-                              static_cast<uint32_t>(run->cfg.seed >> 32)});
-        const uint32_t per_block = kStepWarps * static_cast<uint32_t>(kUnits > 0 ? kUnits : 1);
-        const uint32_t blocks = (run->n_islands + per_block - 1) / per_block;
-        island_units_kernel<5, (kUnits > 0 ? kUnits : 1)><<<blocks, kStepThreads, 0, stream>>>(a);
-        run->launches += 1;
-        return cudaGetLastError();
+    if (run->cfg.mode == GA_SYNC && run->counters_uniform && run->surface_words <= 2) {
+        const uint32_t N = run->cfg.island_size, ts = run->cfg.tournament_size;
+        const bool fit = run->cfg.model == GA_MODEL_FITNESS;
+        StepKernel ku = nullptr;
+        uint32_t islands_per_block = 0;
+        switch (N) {
+        case 16:
+            ku = fit ? (ts == 5 ? island_units_kernel<16, 5, 1> : island_units_kernel<16, 0, 1>)
+                     : (ts == 5 ? island_units_kernel<16, 5, 0> : island_units_kernel<16, 0, 0>);
+            islands_per_block = units_per_block<16>() * 16;
+            break;
+        case 32:
+            ku = fit ? (ts == 5 ? island_units_kernel<32, 5, 1> : island_units_kernel<32, 0, 1>)
+                     : (ts == 5 ? island_units_kernel<32, 5, 0> : island_units_kernel<32, 0, 0>);
+            islands_per_block = units_per_block<32>() * 8;
+            break;
+        case 64:
+            ku = fit ? (ts == 5 ? island_units_kernel<64, 5, 1> : island_units_kernel<64, 0, 1>)
+                     : (ts == 5 ? island_units_kernel<64, 5, 0> : island_units_kernel<64, 0, 0>);
+            islands_per_block = units_per_block<64>() * 8;
+            break;
+        default: break;
+        }
+        if (ku) {
+            StepArgs a;
+            a.r = run_params(run, src, dst, g0, n_gens, migrate);
+            a.rk = round_keys(Key{static_cast<uint32_t>(run->cfg.seed),
+                                  static_cast<uint32_t>(run->cfg.seed >> 32)});
+            const uint32_t blocks = (run->n_islands + islands_per_block - 1) / islands_per_block;
+            ku<<<blocks, kStepThreads, 0, stream>>>(a);
+            run->launches += 1;
+            return cudaGetLastError();
+        }
     }
     StepKernel k =
         uniform ? pick_uniform(run->cfg.island_size, run->surface_words, run->cfg.model) : nullptr;

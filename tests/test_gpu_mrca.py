@@ -62,3 +62,20 @@ def test_two_samples_and_errors():
         g.mrca_bounds(np.array([0, shape.n_agents], np.uint32))
     with pytest.raises(ga.GaError):
         g.mrca_bounds(np.array([0], np.uint32))
+
+
+def test_outputs_at_any_4_byte_alignment():
+    """Output buffers offset by one element from an aligned allocation (4-byte aligned only):
+    the same bounds as the oracle."""
+    import torch
+    g, o, ids = both(SMALL_TORUS, 300, 513, seed=4)
+    n = ids.size
+    pairs = n * (n - 1) // 2
+    dev_ids = torch.from_numpy(np.ascontiguousarray(ids, np.uint32).view(np.int32)).cuda()
+    lo_buf = torch.zeros(pairs + 1, dtype=torch.int32, device="cuda")
+    hi_buf = torch.zeros(pairs + 1, dtype=torch.int32, device="cuda")
+    lo, hi = g.mrca_bounds_device(dev_ids, lo_buf[1:], hi_buf[1:])
+    g.sync()
+    elo, ehi = o.mrca_bounds(ids)
+    assert np.array_equal(lo.cpu().numpy().view(np.uint32), elo)
+    assert np.array_equal(hi.cpu().numpy().view(np.uint32), ehi)

@@ -159,15 +159,16 @@ class Clocks:
 
 
 # Counters of one launch of the island step on the 512x1024x32 grid (migration every
-# generation), from ncu captures of this kernel build (profiles/): DRAM bytes read + written,
+# generation), from an ncu capture of this kernel build on the 256x1024 grid scaled by the
+# islands processed (profiles/): DRAM bytes read + written,
 # warp-instructions per island-generation (smsp__inst_executed.sum / islands), ALU-pipe
 # warp-instructions per island-generation (sm__inst_executed_pipe_alu.sum / islands; each
 # occupies the ALU pipe two cycles) and FMA-heavy pipe cycles per island-generation
 # (sm__pipe_fmaheavy_cycles_active.sum / islands).
-ISLAND_STEP_TRAFFIC = {"kernel": "island_units_kernel<5,8>", "bytes": 449.3e6,
-                       "inst_per_island_gen": 44564480 / 262144,
-                       "alu_inst_per_island_gen": 18513920 / 262144,
-                       "fma_cycles_per_island_gen": 33488896 / 262144,
+ISLAND_STEP_TRAFFIC = {"kernel": "island_units_kernel<32,5,0>", "bytes": 452.6e6,
+                       "inst_per_island_gen": 44335104 / 262144,
+                       "alu_inst_per_island_gen": 16842752 / 262144,
+                       "fma_cycles_per_island_gen": 34078720 / 262144,
                        "rows": 512, "cols": 1024, "island_size": 32}
 # warp-instructions per island-generation of the resident kernel on the 32x32 torus
 # (smsp__inst_executed.sum of a 200-generation launch / (1,024 islands x 200), this build)

@@ -61,11 +61,13 @@ def test_surfaces_and_float_model(S, b, policy):
     o = oracle_for(shape)
     o.step(500)
     assert_same(got, o.snapshot(), 32)
-    fit = RunShape(rows=6, cols=6, model=MODEL_FITNESS, p_del=0.33, p_ben=0.003, seed=18)
-    got = _run(fit, 400, RESIDENT_ON).snapshot()
-    o = oracle_for(fit)
-    o.step(400)
-    assert_same(got, o.snapshot(), 32)
+    for n in (32, 64):
+        fit = RunShape(rows=6, cols=6, island_size=n, model=MODEL_FITNESS, p_del=0.33,
+                       p_ben=0.003, seed=18 + n)
+        got = _run(fit, 400, RESIDENT_ON).snapshot()
+        o = oracle_for(fit)
+        o.step(400)
+        assert_same(got, o.snapshot(), n)
 
 
 def test_split_steps_and_chunk_boundary():

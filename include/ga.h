@@ -252,7 +252,9 @@ int ga_load(ga_run *run, const void *host_src, size_t bytes, uint64_t generation
  * retained ranks at a counter come from the curation rule in closed form, without replaying
  * earlier ranks: O(S) work per distinct table, O(n^2) (GA_SYNC) or O(n^2 S) (mixed
  * counters) for the pairs.
- * Synchronous.  Scratch memory is allocated and freed on the run's stream.
+ * Synchronous.  Scratch memory is taken from and returned to the library's own memory pool
+ * in the run's stream order (one pool per device, which keeps up to 512 MiB mapped across
+ * synchronisations, so repeated calls do not map memory again).
  * Errors: GA_EINVAL (n < 2, n > 65536, id out of range, null pointers), GA_ESTATE
  * (GA_SYNC mode and counters differ), GA_ENOMEM, GA_ECUDA.
  */

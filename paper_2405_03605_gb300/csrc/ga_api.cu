@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "ga_internal.h"
@@ -107,6 +108,39 @@ int take_status(ga_run *run)
 }  // namespace
 
 namespace ga {
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t stream)
+{
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaMallocAsync(p, bytes, stream);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t created;
+            e = cudaMemPoolCreate(&created, &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = kPoolKeepBytes;
+            e = cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(created);
+                return e;
+            }
+            pools[dev] = created;
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, stream);
+}
 
 int step_run(ga_run *run, uint32_t n_gens, cudaStream_t stream)
 {
@@ -416,12 +450,12 @@ int ga_mrca_bounds_device(ga_run *run, const uint32_t *d_agent_ids, uint32_t n, 
     if (!run || !d_agent_ids || !d_lo || !d_hi || n < 2 || n > 65536u) return GA_EINVAL;
     void *scratch = nullptr;
     const size_t bytes = ga::mrca_scratch_bytes(run, n);
-    if (cudaMallocAsync(&scratch, bytes, run->stream) != cudaSuccess) {
+    if (ga::pool_alloc(&scratch, bytes, run->stream) != cudaSuccess) {
         cudaGetLastError();
         return GA_ENOMEM;
     }
     int rc = cuda_rc(ga::launch_mrca(run, d_agent_ids, n, d_lo, d_hi, scratch));
-    const int rc2 = cuda_rc(cudaFreeAsync(scratch, run->stream));
+    const int rc2 = cuda_rc(ga::pool_free(scratch, run->stream));
     return rc != GA_OK ? rc : rc2;
 }
 
@@ -435,7 +469,7 @@ int ga_mrca_bounds(ga_run *run, const uint32_t *agent_ids, uint32_t n, uint32_t 
     const size_t ids_bytes = align_up(n * sizeof(uint32_t), 256);
     const size_t out_bytes = align_up(pairs * sizeof(uint32_t), 256);
     uint8_t *buf = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&buf), ids_bytes + 2 * out_bytes, run->stream) !=
+    if (ga::pool_alloc(reinterpret_cast<void **>(&buf), ids_bytes + 2 * out_bytes, run->stream) !=
         cudaSuccess) {
         cudaGetLastError();
         return GA_ENOMEM;
@@ -452,7 +486,7 @@ int ga_mrca_bounds(ga_run *run, const uint32_t *agent_ids, uint32_t n, uint32_t 
     if (rc == GA_OK)
         rc = cuda_rc(cudaMemcpyAsync(hi, d_hi, pairs * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                      run->stream));
-    cudaFreeAsync(buf, run->stream);
+    ga::pool_free(buf, run->stream);
     if (cudaStreamSynchronize(run->stream) != cudaSuccess) return GA_ECUDA;
     if (rc != GA_OK) return rc;
     return take_status(run);

@@ -271,19 +271,19 @@ namespace {
 
 int rc_of(cudaError_t e) { return e == cudaSuccess ? GA_OK : GA_ECUDA; }
 
-// Device tables are allocated and freed in the batch stream's order (cudaMallocAsync /
-// cudaFreeAsync), so a rebuild never waits for the launches already queued: they finish with
+// Device tables are allocated and freed in the batch stream's order (the library's memory
+// pool, stream-ordered), so a rebuild never waits for the launches already queued: they finish with
 // the tables they were given before those are freed.
 void free_device(ga_batch *b)
 {
     for (auto &c : b->classes) {
-        if (c.d_unit_run) cudaFreeAsync(c.d_unit_run, b->stream);
-        if (c.d_unit_local) cudaFreeAsync(c.d_unit_local, b->stream);
+        if (c.d_unit_run) ga::pool_free(c.d_unit_run, b->stream);
+        if (c.d_unit_local) ga::pool_free(c.d_unit_local, b->stream);
         c.d_unit_run = c.d_unit_local = nullptr;
     }
-    if (b->d_runs) cudaFreeAsync(b->d_runs, b->stream);
-    if (b->d_sites) cudaFreeAsync(b->d_sites, b->stream);
-    if (b->d_masks) cudaFreeAsync(b->d_masks, b->stream);
+    if (b->d_runs) ga::pool_free(b->d_runs, b->stream);
+    if (b->d_sites) ga::pool_free(b->d_sites, b->stream);
+    if (b->d_masks) ga::pool_free(b->d_masks, b->stream);
     b->d_runs = nullptr;
     b->d_sites = nullptr;
     b->d_masks = nullptr;
@@ -409,7 +409,7 @@ int rebuild(ga_batch *b)
     }
     // pageable host sources: each copy is staged before the call returns, so the host vectors
     // may go out of scope without a wait
-    if (cudaMallocAsync(reinterpret_cast<void **>(&b->d_runs), n * sizeof(ga::RunDesc), b->stream) !=
+    if (ga::pool_alloc(reinterpret_cast<void **>(&b->d_runs), n * sizeof(ga::RunDesc), b->stream) !=
         cudaSuccess)
         return GA_ENOMEM;
     int rc = rc_of(cudaMemcpyAsync(b->d_runs, desc.data(), n * sizeof(ga::RunDesc),
@@ -426,9 +426,9 @@ int rebuild(ga_batch *b)
             }
         }
         c.units = static_cast<uint32_t>(ur.size());
-        if (cudaMallocAsync(reinterpret_cast<void **>(&c.d_unit_run), ur.size() * 4, b->stream) !=
+        if (ga::pool_alloc(reinterpret_cast<void **>(&c.d_unit_run), ur.size() * 4, b->stream) !=
                 cudaSuccess ||
-            cudaMallocAsync(reinterpret_cast<void **>(&c.d_unit_local), ul.size() * 4, b->stream) !=
+            ga::pool_alloc(reinterpret_cast<void **>(&c.d_unit_local), ul.size() * 4, b->stream) !=
                 cudaSuccess)
             return GA_ENOMEM;
         rc = rc_of(cudaMemcpyAsync(c.d_unit_run, ur.data(), ur.size() * 4, cudaMemcpyHostToDevice,
@@ -458,14 +458,14 @@ bool members_moved(const ga_batch *b)
 int ensure_sites(ga_batch *b, uint32_t chunk)
 {
     if (b->sites_cap >= chunk) return GA_OK;
-    if (b->d_sites) cudaFreeAsync(b->d_sites, b->stream);
-    if (b->d_masks) cudaFreeAsync(b->d_masks, b->stream);
+    if (b->d_sites) ga::pool_free(b->d_sites, b->stream);
+    if (b->d_masks) ga::pool_free(b->d_masks, b->stream);
     b->d_sites = nullptr;
     b->d_masks = nullptr;
     const size_t entries = b->runs.size() * static_cast<size_t>(chunk);
-    if (cudaMallocAsync(reinterpret_cast<void **>(&b->d_sites), entries * sizeof(int32_t), b->stream) !=
+    if (ga::pool_alloc(reinterpret_cast<void **>(&b->d_sites), entries * sizeof(int32_t), b->stream) !=
             cudaSuccess ||
-        cudaMallocAsync(reinterpret_cast<void **>(&b->d_masks), entries * sizeof(uint2), b->stream) !=
+        ga::pool_alloc(reinterpret_cast<void **>(&b->d_masks), entries * sizeof(uint2), b->stream) !=
             cudaSuccess)
         return GA_ENOMEM;
     b->sites_cap = chunk;

@@ -46,6 +46,15 @@ struct ga_run {
 
 namespace ga {
 
+// Stream-ordered device memory of the library (per-call scratch, batch tables): a memory pool
+// of the library's own on each device, created on first use, which keeps up to
+// kPoolKeepBytes reserved across synchronisations.  The device's default pool returns freed
+// memory at every synchronisation, so a caller that synchronises between calls would pay for
+// mapping the memory again on each call.
+constexpr uint64_t kPoolKeepBytes = 512ull << 20;
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t stream);
+inline cudaError_t pool_free(void *p, cudaStream_t stream) { return cudaFreeAsync(p, stream); }
+
 // Launch `kernel` as a programmatic dependent of the previous kernel on `stream` (see
 // wait_previous_grid in ga_device.cuh).
 template <typename... P, typename... A>

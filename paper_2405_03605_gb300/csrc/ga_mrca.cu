@@ -1,19 +1,22 @@
 // ga_mrca.cu -- pairwise MRCA bounds over sampled end-state agents (post hoc relatedness
 // estimation from hstrat markers, Fig. 1 caption of the paper).
 //
-// Pipeline (all on the run's stream):
-//   1. rank_table_kernel: the ranks the surface retains at counter T, in closed form (no
-//                      replay of ranks 0..T-1): one thread per retained rank (steady) or per
-//                      site (tilted), each rank placed at its site; then the occupied sites
-//                      sorted by rank in the same block (S <= 256): r_1 < ... < r_m.
-//   2. pack_kernel   : gather each sampled agent's differentiae in rank order into a bit
-//                      string (differentia i at bits [i*b, i*b + b)), 8 words per agent; one
-//                      warp per agent, one warp OR-reduction per packed word.
-//   3. pair_kernel   : one thread per pair (i, j), j > i, in output order; the first set bit of
-//                      packed[i] ^ packed[j] gives the first mismatching rank index i*,
-//                      from which hi = r_{i*} and lo = r_{i*-K} + 1 (0 if i* <= K); with no
-//                      mismatch hi = T, lo = r_{m-K+1} + 1 (0 if m < K).
-// The pair kernel is bound by its output: 8 bytes (lo, hi) per pair, written once with
+// Pipeline (all on the run's stream).  Strings of at most 64 bits (S b <= 64), two launches:
+//   1. pack64_kernel : one thread per sampled agent; each block first finds the ranks the
+//                      surface retains at counter T in closed form (no replay of ranks
+//                      0..T-1: one thread per retained rank or site) and sorts the occupied
+//                      sites by rank, r_0 < ... < r_{m-1} (block 0 also writes them out for
+//                      the pair kernel); each thread then gathers its agent's differentiae in
+//                      rank order into one 64-bit string, stored bit-reversed (the first rank
+//                      index at bit 63), 8 bytes per agent.
+//   2. pair64_kernel : one thread per pair (i, j), j > i, in output order; the count of
+//                      leading zeros of packed[i] ^ packed[j] gives the first mismatching
+//                      rank index i*, from which hi = r_{i*} and lo = r_{i*-K} + 1 (0 if
+//                      i* < K); with no mismatch hi = T, lo = r_{m-K} + 1 (0 if m < K).
+// Wider strings (up to 256 bits), three launches: rank_table_kernel (the same closed form,
+// once), pack_kernel (one warp per agent, 8 words), pair_kernel (the first nonzero word of the
+// XOR, then the same rules).
+// The pair kernels are bound by their output: 8 bytes (lo, hi) per pair, written once with
 // streaming stores.
 #include "ga_device.cuh"
 #include "ga_internal.h"
@@ -25,13 +28,14 @@ namespace {
 constexpr uint32_t kPackWords = 8;  // 256-bit rank-ordered strings
 constexpr int kPairThreads = 256;
 constexpr unsigned long long kPairGrid = 152ull * 8ull;  // 8 resident blocks on each of 152 SMs
+constexpr uint32_t kPack64Threads = 128;  // >= 64 sites; small blocks spread a sample over SMs
 
 
 struct MrcaLayout {
     uint32_t *order;   // [S]  sites sorted by rank
     uint32_t *ranks;   // [S]  sorted ranks
     uint32_t *meta;    // [4]  m
-    uint32_t *packed;  // [n][kPackWords]
+    uint32_t *packed;  // [n][kPackWords] (strings of at most 64 bits: [n] 64-bit words)
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -175,14 +179,11 @@ cudaError_t launch_rank_table(uint32_t *order, uint32_t *ranks, uint32_t *meta, 
 // One warp per sampled agent: lanes 0..7 hold the agent's surface words; for packed word w,
 // lane l gathers differentia index w * (32/b) + l (site order[i], fetched from the lane that
 // holds its surface word) and one warp OR-reduction assembles the word.
-// reverse64 (strings of at most 64 bits): the 64-bit string (word 1 : word 0) is stored
-// bit-reversed, so the first rank index sits at bit 63 and a pair's first mismatch is the
-// count of leading zeros of the XOR.
 __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_words,
                             uint32_t n_agents, const uint32_t *__restrict__ ids, uint32_t n,
                             const uint32_t *__restrict__ order, const uint32_t *__restrict__ meta,
                             uint32_t bits, uint32_t T, uint32_t *__restrict__ packed,
-                            int *__restrict__ status, uint32_t reverse64)
+                            int *__restrict__ status)
 {
     __shared__ uint32_t ord[256];
     release_next_grid();  // the pair kernel may start its index set-up
@@ -215,38 +216,162 @@ __global__ void pack_kernel(const uint32_t *__restrict__ pop, uint32_t record_wo
             if (lane == w) word_out = full;
         }
     }
-    if (reverse64) {  // lanes 0 and 1 swap words and reverse their bits
-        const uint32_t other = __shfl_xor_sync(0xffffffffu, word_out, 1);
-        if (lane < 2u) word_out = __brev(other);
-    }
     if (lane < kPackWords) packed[static_cast<size_t>(a) * kPackWords + lane] = word_out;
 }
 
-// Pairs in output order, each warp a contiguous stretch of them: lane t takes pairs
-// base + t, base + t + 32, ..., so a warp's (lo, hi) writes are contiguous.  A lane finds
-// the row of its first pair once -- row i holds pairs off(i) <= p < off(i + 1) with
-// off(i) = i (2n - i - 1) / 2; a single-precision root of i^2 - (2n - 1) i + 2p = 0 from the
-// exact 64-bit discriminant is within one row, and integer comparisons correct it -- then
-// steps 32 pairs at a time, carrying into the next rows when j passes n - 1, and reloads row
-// i's string only when i changes.  Pair indices fit 32 bits (n <= 65536: fewer than 2^31
-// pairs).  The first set bit of packed[i] ^ packed[j] gives the first mismatching rank index
-// i*.  With 0-based sorted ranks r_0 < ... < r_{m-1}, a mismatch at index i* gives
-// hi = r_{i*}, lo = r_{i*-K} + 1 (0 if i* < K), and no mismatch hi = T, lo = r_{m-K} + 1.
-// 64-bit strings (S*b <= 64) are stored bit-reversed (pack_kernel): a pair's first mismatching
-// bit is the count c of leading zeros of the XOR, 64 when none (the bits past m*b are zero in
-// every string), and one shared table holds both bounds for every c in [0, 64]:
-// i* = min(c / b, m), tab[c] = (i* >= K ? r_{i*-K} + 1 : 0, i* < m ? r_{i*} : T).  WIDE
-// strings (more than 64 bits) take the first nonzero word of the XOR and the two rules
-// separately (measured faster for them than a table).
-template <bool WIDE>
+// Row and column of pair p in output order: row i holds pairs off(i) <= p < off(i + 1) with
+// off(i) = i (2n - i - 1) / 2.  A single-precision root of i^2 - (2n - 1) i + 2p = 0 from the
+// exact 64-bit discriminant is within one row; integer comparisons correct it.
+__device__ __forceinline__ void first_pair(uint32_t n, uint32_t p, uint32_t &i, uint32_t &j)
+{
+    const unsigned long long b = 2ull * n - 1ull;  // off(r) = r (b - r) / 2
+    const float est = (static_cast<float>(b) - sqrtf(static_cast<float>(b * b - 8ull * p))) * 0.5f;
+    i = est > 0.0f ? static_cast<uint32_t>(est) : 0u;
+    if (i > n - 2u) i = n - 2u;
+    while (i > 0u && static_cast<unsigned long long>(i) * (b - i) / 2ull > p) --i;
+    while (i + 2u < n && static_cast<unsigned long long>(i + 1u) * (b - i - 1u) / 2ull <= p) ++i;
+    j = i + 1u + static_cast<uint32_t>(p - static_cast<unsigned long long>(i) * (b - i) / 2ull);
+}
+
+// Strings of at most 64 bits: one thread per sampled agent.  Each block first builds the
+// rank order itself (threads k < S: retained entry k in closed form, placed at its site; the
+// occupied sites then sorted by rank), so no launch precedes this one; block 0 also writes the
+// sorted ranks and m for the pair kernel.  Thread a then reads agent ids[a]'s 64-bit surface
+// (differentia at site k in bits [k b, k b + b)) and assembles the string with differentia
+// index i at bits [i b, i b + b), stored bit-reversed: the first rank index at bit 63, so a
+// pair's first mismatch is the count of leading zeros of the XOR.  Bits past m b stay zero.
+__global__ void __launch_bounds__(kPack64Threads)
+pack64_kernel(const uint32_t *__restrict__ pop, uint32_t record_words, uint32_t n_agents,
+              const uint32_t *__restrict__ ids, uint32_t n, uint32_t policy, uint32_t log2_sites,
+              uint32_t sites, uint32_t bits, uint32_t T, uint32_t *__restrict__ ranks,
+              uint32_t *__restrict__ meta, unsigned long long *__restrict__ packed,
+              int *__restrict__ status)
+{
+    __shared__ __align__(16) uint32_t h[64];
+    __shared__ uint32_t shift[64];  // surface bit offset of differentia index i
+    release_next_grid();  // the pair kernel may start its index set-up
+    const uint32_t k = threadIdx.x;
+    const uint32_t a = blockIdx.x * blockDim.x + k;
+    const uint32_t id = a < n ? ids[a] : 0u;
+    const bool ok = a < n && id < n_agents;
+    const uint32_t *rec = pop + static_cast<size_t>(ok ? id : 0u) * record_words;
+    const uint32_t counter = ok ? rec[1] : T;
+    const uint32_t w0 = ok ? rec[2] : 0u;
+    const uint32_t w1 = (ok && record_words > 3u) ? rec[3] : 0u;
+    if (k < 64u) h[k] = 0u;
+    __syncthreads();
+    if (k < sites) {
+        uint32_t site = 0;
+        const uint32_t r1 = retained_entry(policy, log2_sites, sites, T, k, site);
+        if (r1 != 0u && in_bounds(site < sites, status)) h[site] = r1;
+    }
+    __syncthreads();
+    const uint32_t mine = k < sites ? h[k] : 0u;
+    const uint32_t m = static_cast<uint32_t>(__syncthreads_count(mine != 0u));
+    if (mine != 0u) {  // position among the occupied sites, all 64 entries read at once
+        uint32_t pos = 0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const uint4 v = reinterpret_cast<const uint4 *>(h)[q];
+            pos += (v.x != 0u && v.x < mine) + (v.y != 0u && v.y < mine) +
+                   (v.z != 0u && v.z < mine) + (v.w != 0u && v.w < mine);
+        }
+        shift[pos] = k * bits;
+        if (blockIdx.x == 0) ranks[pos] = mine - 1u;
+    }
+    if (blockIdx.x == 0 && k == 0) meta[0] = m;
+    __syncthreads();
+    if (a >= n) return;
+    if (!ok) {
+        atomicCAS(status, GA_OK, GA_EINVAL);
+        packed[a] = 0ull;
+        return;
+    }
+    if (counter != T) atomicCAS(status, GA_OK, GA_ESTATE);
+    // differentia index i goes to bits [i b, i b + b) of (o1 : o0); a differentia never
+    // straddles a surface word (b divides 32)
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t o0 = 0u, o1 = 0u;
+#pragma unroll 8
+    for (uint32_t i = 0; i < m; ++i) {
+        const uint32_t sh = shift[i];
+        const uint32_t v = (((sh & 32u) ? w1 : w0) >> (sh & 31u)) & mask;
+        const uint32_t ob = i * bits;
+        if (ob & 32u) o1 |= v << (ob & 31u);
+        else o0 |= v << (ob & 31u);
+    }
+    // bit-reversed 64-bit string: reverse(o1 : o0) = reverse(o0) : reverse(o1)
+    packed[a] = (static_cast<unsigned long long>(__brev(o0)) << 32) | __brev(o1);
+}
+
+// Pairs of 64-bit strings, in output order, each warp a contiguous stretch of them: lane t
+// takes pairs base + t, base + t + 32, ... (the row of its first pair found as in pair_kernel
+// below), steps 32 pairs at a time and reloads row i's string only when a step carries it into
+// the next rows.  tab[c] holds both bounds for a leading-zero count c in [0, 64]:
+// i* = min(c / b, m), tab[c] = (i* >= K ? r_{i*-K} + 1 : 0, i* < m ? r_{i*} : T).
+__global__ void __launch_bounds__(kPairThreads)
+pair64_kernel(const unsigned long long *__restrict__ packed, uint32_t n,
+              const uint32_t *__restrict__ ranks_g, const uint32_t *__restrict__ meta,
+              uint32_t log2_bits, uint32_t K, uint32_t T, uint32_t per_warp,
+              uint32_t *__restrict__ lo, uint32_t *__restrict__ hi, int *__restrict__ status)
+{
+    __shared__ uint2 tab[65];
+    const uint32_t n_pairs = n * (n - 1u) / 2u;
+    const uint32_t warp = (blockIdx.x * kPairThreads + threadIdx.x) >> 5;
+    const unsigned long long w_end = static_cast<unsigned long long>(warp + 1u) * per_warp;
+    const uint32_t p_end = w_end < n_pairs ? static_cast<uint32_t>(w_end) : n_pairs;
+    const unsigned long long p0 = static_cast<unsigned long long>(warp) * per_warp + (threadIdx.x & 31u);
+    const bool active = p0 < p_end;
+    const uint32_t p = active ? static_cast<uint32_t>(p0) : 0u;
+    uint32_t i = 0, j = 1;
+    first_pair(n, p, i, j);
+
+    wait_previous_grid();  // ranks, m and the strings come from pack64_kernel
+    const uint32_t m = meta[0];
+    for (uint32_t c = threadIdx.x; c <= 64u; c += blockDim.x) {
+        uint32_t r = c >> log2_bits;
+        r = r < m ? r : m;
+        tab[c] = make_uint2(r >= K ? ranks_g[r - K] + 1u : 0u, r < m ? ranks_g[r] : T);
+    }
+    __syncthreads();
+    if (!active || !in_bounds(i < j && j < n, status)) return;
+
+    unsigned long long row = __ldg(packed + i);
+    for (uint32_t q = p;;) {
+        const unsigned long long x = __ldg(packed + j) ^ row;
+        const uint2 bound = tab[__clzll(static_cast<long long>(x))];  // first differing bit, 64: none
+        __stcs(lo + q, bound.x);
+        __stcs(hi + q, bound.y);
+        q += 32u;
+        if (q >= p_end) break;
+        j += 32u;
+        if (j >= n) {  // past the end of row i: pair (i + 1, i + 2) follows (i, n - 1)
+            do {
+                j = j - n + i + 2u;
+                ++i;
+            } while (j >= n);
+            if (!in_bounds(i < j, status)) break;
+            row = __ldg(packed + i);
+        }
+    }
+}
+
+// Pairs of strings wider than 64 bits, in output order, each warp a contiguous stretch of
+// them: lane t takes pairs base + t, base + t + 32, ..., so a warp's (lo, hi) writes are
+// contiguous.  A lane finds the row of its first pair once (first_pair), then steps 32 pairs
+// at a time, carrying into the next rows when j passes n - 1, and reloads row i's string only
+// when i changes.  Pair indices fit 32 bits (n <= 65536: fewer than 2^31 pairs).  The first
+// set bit of packed[i] ^ packed[j] (the first nonzero word, then its lowest set bit) gives the
+// first mismatching rank index i*.  With 0-based sorted ranks r_0 < ... < r_{m-1}, a mismatch
+// at index i* gives hi = r_{i*}, lo = r_{i*-K} + 1 (0 if i* < K), and no mismatch hi = T,
+// lo = r_{m-K} + 1.
 __global__ void __launch_bounds__(kPairThreads)
 pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__restrict__ ranks_g,
             const uint32_t *__restrict__ meta, uint32_t log2_bits, uint32_t K, uint32_t T,
             uint32_t per_warp, uint32_t *__restrict__ lo, uint32_t *__restrict__ hi,
             int *__restrict__ status)
 {
-    __shared__ uint2 tab[WIDE ? 1 : 65];
-    __shared__ uint32_t ranks[WIDE ? 256 : 1];
+    __shared__ uint32_t ranks[256];
     // pairs [warp * per_warp, (warp + 1) * per_warp) of n (n - 1) / 2 (per_warp: a multiple of
     // 32 chosen on the host so that the grid covers every pair)
     const uint32_t n_pairs = n * (n - 1u) / 2u;
@@ -256,78 +381,50 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
     const unsigned long long p0 = static_cast<unsigned long long>(warp) * per_warp + (threadIdx.x & 31u);
     const bool active = p0 < p_end;
     const uint32_t p = active ? static_cast<uint32_t>(p0) : 0u;
-
-    const unsigned long long b = 2ull * n - 1ull;  // off(r) = r (b - r) / 2
-    const float est = (static_cast<float>(b) - sqrtf(static_cast<float>(b * b - 8ull * p))) * 0.5f;
-    uint32_t i = est > 0.0f ? static_cast<uint32_t>(est) : 0u;
-    if (i > n - 2u) i = n - 2u;
-    while (i > 0u && static_cast<unsigned long long>(i) * (b - i) / 2ull > p) --i;
-    while (i + 2u < n && static_cast<unsigned long long>(i + 1u) * (b - i - 1u) / 2ull <= p) ++i;
-    uint32_t j = i + 1u + static_cast<uint32_t>(p - static_cast<unsigned long long>(i) * (b - i) / 2ull);
+    uint32_t i = 0, j = 1;
+    first_pair(n, p, i, j);
     uint32_t q = p;
-    const uint32_t q_end = p_end;
     uint32_t *lo_q = lo + q;
     uint32_t *hi_q = hi + q;
 
     // the rank table and the packed strings come from the kernels before this one
     wait_previous_grid();
     const uint32_t m = meta[0];
-    if constexpr (!WIDE) {
-        for (uint32_t c = threadIdx.x; c <= 64u; c += blockDim.x) {
-            uint32_t r = c >> log2_bits;
-            r = r < m ? r : m;
-            tab[c] = make_uint2(r >= K ? ranks_g[r - K] + 1u : 0u, r < m ? ranks_g[r] : T);
-        }
-    } else {
-        for (uint32_t r = threadIdx.x; r < m; r += blockDim.x) ranks[r] = ranks_g[r];
-    }
+    for (uint32_t r = threadIdx.x; r < m; r += blockDim.x) ranks[r] = ranks_g[r];
     __syncthreads();
     if (!active) return;
 
-    uint32_t row = 0xFFFFFFFFu;  // row whose string a0n (or a0, a1) holds
-    unsigned long long a0n = 0ull;
+    uint32_t row = 0xFFFFFFFFu;  // row whose string a0, a1 hold
     uint4 a0 = make_uint4(0u, 0u, 0u, 0u), a1 = a0;
     for (;;) {
         if (!in_bounds(i < j && j < n, status)) break;
         if (i != row) {
-            if constexpr (!WIDE) {
-                a0n = __ldg(reinterpret_cast<const unsigned long long *>(packed) + i * (kPackWords / 2u));
-            } else {
-                a0 = __ldg(reinterpret_cast<const uint4 *>(packed) + i * (kPackWords / 4u));
-                a1 = __ldg(reinterpret_cast<const uint4 *>(packed) + i * (kPackWords / 4u) + 1u);
-            }
+            a0 = __ldg(reinterpret_cast<const uint4 *>(packed) + i * (kPackWords / 4u));
+            a1 = __ldg(reinterpret_cast<const uint4 *>(packed) + i * (kPackWords / 4u) + 1u);
             row = i;
         }
-        if constexpr (!WIDE) {
-            const unsigned long long x =
-                __ldg(reinterpret_cast<const unsigned long long *>(packed) + j * (kPackWords / 2u)) ^ a0n;
-            const uint2 bound = tab[__clzll(static_cast<long long>(x))];  // first differing bit, 64: none
-            __stcs(lo_q, bound.x);
-            __stcs(hi_q, bound.y);
-        } else {
-            const uint4 b0 = __ldg(reinterpret_cast<const uint4 *>(packed) + j * (kPackWords / 4u));
-            const uint4 b1 = __ldg(reinterpret_cast<const uint4 *>(packed) + j * (kPackWords / 4u) + 1u);
-            const uint32_t x[kPackWords] = {b0.x ^ a0.x, b0.y ^ a0.y, b0.z ^ a0.z, b0.w ^ a0.w,
-                                            b1.x ^ a1.x, b1.y ^ a1.y, b1.z ^ a1.z, b1.w ^ a1.w};
-            uint32_t first_bit = 0xFFFFFFFFu;
+        const uint4 b0 = __ldg(reinterpret_cast<const uint4 *>(packed) + j * (kPackWords / 4u));
+        const uint4 b1 = __ldg(reinterpret_cast<const uint4 *>(packed) + j * (kPackWords / 4u) + 1u);
+        const uint32_t x[kPackWords] = {b0.x ^ a0.x, b0.y ^ a0.y, b0.z ^ a0.z, b0.w ^ a0.w,
+                                        b1.x ^ a1.x, b1.y ^ a1.y, b1.z ^ a1.z, b1.w ^ a1.w};
+        uint32_t first_bit = 0xFFFFFFFFu;
 #pragma unroll
-            for (int w = kPackWords - 1; w >= 0; --w)
-                if (x[w] != 0u) first_bit = 32u * w + (__ffs(x[w]) - 1u);
-            uint32_t l, h;
-            if (first_bit == 0xFFFFFFFFu) {
-                h = T;
-                l = m >= K ? ranks[m - K] + 1u : 0u;
-            } else {
-                uint32_t istar = first_bit >> log2_bits;  // first mismatch, 0-based
-                if (!in_bounds(istar < m, status)) istar = 0u;
-                h = ranks[istar];
-                l = istar >= K ? ranks[istar - K] + 1u : 0u;
-            }
-            __stcs(lo_q, l);
-            __stcs(hi_q, h);
+        for (int w = kPackWords - 1; w >= 0; --w)
+            if (x[w] != 0u) first_bit = 32u * w + (__ffs(x[w]) - 1u);
+        uint32_t l, h;
+        if (first_bit == 0xFFFFFFFFu) {
+            h = T;
+            l = m >= K ? ranks[m - K] + 1u : 0u;
+        } else {
+            uint32_t istar = first_bit >> log2_bits;  // first mismatch, 0-based
+            if (!in_bounds(istar < m, status)) istar = 0u;
+            h = ranks[istar];
+            l = istar >= K ? ranks[istar - K] + 1u : 0u;
         }
+        __stcs(lo_q, l);
+        __stcs(hi_q, h);
         q += 32u;
-        if (q >= q_end) break;
+        if (q >= p_end) break;
         lo_q += 32;
         hi_q += 32;
         j += 32u;
@@ -338,32 +435,63 @@ pair_kernel(const uint32_t *__restrict__ packed, uint32_t n, const uint32_t *__r
     }
 }
 
-// pack + pair launches shared by the allocating and the fixed-scratch entry points; both are
-// programmatically dependent launches (each starts its independent set-up while the kernel
-// before it finishes)
-cudaError_t launch_pack_and_pairs(const uint32_t *pop, uint32_t record_words, uint32_t n_agents,
-                           const uint32_t *d_ids, uint32_t n, const uint32_t *order,
-                           const uint32_t *ranks, const uint32_t *meta, uint32_t sites,
-                           uint32_t bits, uint32_t K, uint32_t T, uint32_t *packed,
-                           uint32_t *d_lo, uint32_t *d_hi, int *status, cudaStream_t stream)
+// Grid and stretch length of a pair kernel: enough resident blocks for the whole GPU, each
+// warp then sweeping a contiguous stretch of pairs (a multiple of 32).
+void pair_grid(uint32_t n, uint32_t &grid, uint32_t &per_warp)
 {
-    // sites * bits <= 64: every rank-ordered string fits in its first 64 bits (bit-reversed)
-    const bool narrow = sites * bits <= 64u;
-    const cudaError_t e = launch_dependent(pack_kernel, (n + 7u) / 8u, 256, stream, pop,
-                                           record_words, n_agents, d_ids, n, order, meta, bits, T,
-                                           packed, status, narrow ? 1u : 0u);
-    if (e != cudaSuccess) return e;
-    // enough resident blocks for the whole GPU, each thread then sweeping several pairs
     const unsigned long long pairs = static_cast<unsigned long long>(n) * (n - 1u) / 2ull;
     const unsigned long long want = (pairs + kPairThreads - 1) / kPairThreads;
-    const uint32_t grid = static_cast<uint32_t>(want < kPairGrid ? want : kPairGrid);
+    grid = static_cast<uint32_t>(want < kPairGrid ? want : kPairGrid);
     const unsigned long long n_warps = static_cast<unsigned long long>(grid) * (kPairThreads / 32);
-    const uint32_t per_warp =
-        static_cast<uint32_t>(((pairs + n_warps - 1ull) / n_warps + 31ull) / 32ull * 32ull);
+    per_warp = static_cast<uint32_t>(((pairs + n_warps - 1ull) / n_warps + 31ull) / 32ull * 32ull);
+}
+
+uint32_t margin(uint32_t bits);
+
+// Every launch of one synchronous MRCA call (shared by the allocating and the fixed-scratch
+// entry points): two for strings of at most 64 bits (pack64, then pair64 as a programmatically
+// dependent launch), three otherwise (rank table, then pack and pair as dependent launches).
+cudaError_t launch_sync_mrca(const uint32_t *pop, uint32_t record_words, uint32_t n_agents,
+                             const uint32_t *d_ids, uint32_t n, const MrcaLayout &l,
+                             uint32_t policy, uint32_t log2_sites, uint32_t sites, uint32_t bits,
+                             uint32_t T, uint32_t *d_lo, uint32_t *d_hi, int *status,
+                             cudaStream_t stream, uint32_t &launches)
+{
+    const uint32_t K = margin(bits);
     const uint32_t log2_bits = bits == 1u ? 0u : bits == 2u ? 1u : bits == 4u ? 2u : 3u;
-    return launch_dependent(narrow ? pair_kernel<false> : pair_kernel<true>, grid,
-                            kPairThreads, stream, packed, n, ranks, meta, log2_bits, K, T, per_warp,
-                            d_lo, d_hi, status);
+    uint32_t grid = 0, per_warp = 0;
+    pair_grid(n, grid, per_warp);
+    unsigned long long *packed64 = reinterpret_cast<unsigned long long *>(l.packed);
+    if (sites * bits <= 64u) {
+        pack64_kernel<<<(n + kPack64Threads - 1u) / kPack64Threads, kPack64Threads, 0, stream>>>(
+            pop, record_words, n_agents, d_ids, n, policy, log2_sites, sites, bits, T, l.ranks,
+            l.meta, packed64, status);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        launches += 1;
+        e = launch_dependent(pair64_kernel, grid, kPairThreads, stream,
+                             static_cast<const unsigned long long *>(packed64), n,
+                             static_cast<const uint32_t *>(l.ranks),
+                             static_cast<const uint32_t *>(l.meta), log2_bits, K, T, per_warp,
+                             d_lo, d_hi, status);
+        if (e == cudaSuccess) launches += 1;
+        return e;
+    }
+    cudaError_t e = launch_rank_table(l.order, l.ranks, l.meta, policy, log2_sites, sites, T, stream);
+    if (e != cudaSuccess) return e;
+    launches += 1;
+    e = launch_dependent(pack_kernel, (n + 7u) / 8u, 256, stream, pop, record_words, n_agents,
+                         d_ids, n, static_cast<const uint32_t *>(l.order),
+                         static_cast<const uint32_t *>(l.meta), bits, T, l.packed, status);
+    if (e != cudaSuccess) return e;
+    launches += 1;
+    e = launch_dependent(pair_kernel, grid, kPairThreads, stream,
+                         static_cast<const uint32_t *>(l.packed), n,
+                         static_cast<const uint32_t *>(l.ranks),
+                         static_cast<const uint32_t *>(l.meta), log2_bits, K, T, per_warp, d_lo,
+                         d_hi, status);
+    if (e == cudaSuccess) launches += 1;
+    return e;
 }
 
 uint32_t margin(uint32_t bits)
@@ -553,16 +681,13 @@ cudaError_t launch_mrca(ga_run *run, const uint32_t *d_ids, uint32_t n, uint32_t
     const uint32_t S = run->cfg.surface_sites, b = run->cfg.differentia_bits;
     const uint32_t T = static_cast<uint32_t>(run->generation);
     MrcaLayout l = carve(scratch, S);
-    cudaError_t e0 = launch_rank_table(l.order, l.ranks, l.meta, run->cfg.curation,
-                                       run->log2_sites, S, T, run->stream);
-    if (e0 != cudaSuccess) return e0;
-    run->launches += 1;
-    const cudaError_t e = launch_pack_and_pairs(
+    uint32_t launches = 0;
+    const cudaError_t e = launch_sync_mrca(
         reinterpret_cast<const uint32_t *>(run->pop[run->cur]), run->record_bytes / 4u,
-        run->n_agents, d_ids, n, l.order, l.ranks, l.meta, S, b, margin(b), T, l.packed, d_lo,
-        d_hi, run->d_status, run->stream);
+        run->n_agents, d_ids, n, l, run->cfg.curation, run->log2_sites, S, b, T, d_lo, d_hi,
+        run->d_status, run->stream, launches);
+    run->launches += launches;
     if (e != cudaSuccess) return e;
-    run->launches += 2;
     return cudaGetLastError();
 }
 
@@ -631,12 +756,10 @@ extern "C" int ga_mrca_bounds_noalloc(const void *d_records, uint32_t record_byt
     while ((1u << log2_sites) < S) ++log2_sites;
 
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return GA_ECUDA;
-    if (launch_rank_table(l.order, l.ranks, l.meta, curation, log2_sites, S, generation, st) !=
-        cudaSuccess)
-        return GA_ECUDA;
-    if (launch_pack_and_pairs(static_cast<const uint32_t *>(d_records), record_bytes / 4u,
-                              n_agents, d_agent_ids, n, l.order, l.ranks, l.meta, S, b, margin(b),
-                              generation, l.packed, d_lo, d_hi, status, st) != cudaSuccess)
+    uint32_t launches = 0;
+    if (launch_sync_mrca(static_cast<const uint32_t *>(d_records), record_bytes / 4u, n_agents,
+                         d_agent_ids, n, l, curation, log2_sites, S, b, generation, d_lo, d_hi,
+                         status, st, launches) != cudaSuccess)
         return GA_ECUDA;
     int device_status = GA_OK;
     if (cudaMemcpyAsync(&device_status, status, sizeof(int), cudaMemcpyDeviceToHost, st) !=

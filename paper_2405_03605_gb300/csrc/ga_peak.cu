@@ -125,7 +125,7 @@ extern "C" int ga_int_peak(uint32_t kind, uint32_t iters, void *stream, double *
         return GA_ECUDA;
     const uint32_t blocks = static_cast<uint32_t>(sms) * 8u;  // 64 resident warps per SM
     uint32_t *sink = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&sink), 256 * sizeof(uint32_t), st) != cudaSuccess) {
+    if (pool_alloc(reinterpret_cast<void **>(&sink), 256 * sizeof(uint32_t), st) != cudaSuccess) {
         cudaGetLastError();
         return GA_ENOMEM;
     }
@@ -150,7 +150,7 @@ extern "C" int ga_int_peak(uint32_t kind, uint32_t iters, void *stream, double *
     if (rc == GA_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = GA_ECUDA;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaFreeAsync(sink, st);
+    pool_free(sink, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) rc = GA_ECUDA;
     if (rc != GA_OK) return rc;
     // operations of the timed launch per iteration and thread: 8 chains x 32 steps (LOP3,

@@ -39,6 +39,23 @@ def test_variant_pairs(name):
     assert np.array_equal(hi, ehi)
 
 
+@pytest.mark.parametrize("S,b,policy,n_ids", [
+    (16, 4, "TILTED", 1500), (32, 2, "STEADY", 777), (8, 8, "HYBRID", 301), (4, 1, "STEADY", 64),
+    (64, 1, "STEADY", 4096),
+])
+def test_narrow_strings(S, b, policy, n_ids):
+    """Strings of at most 64 bits (the two-launch path): every curation policy, differentia
+    widths 1 to 8, samples spanning several pack blocks, and the full 4,096-agent sample."""
+    from paper_2405_03605_gb300 import workloads
+    shape = RunShape(rows=16, cols=10, surface_sites=S, differentia_bits=b,
+                     curation=getattr(workloads, policy), seed=S + b)
+    g, o, ids = both(shape, 900, n_ids, seed=S)
+    lo, hi = g.mrca_bounds(ids)
+    elo, ehi = o.mrca_bounds(ids)
+    assert np.array_equal(lo, elo)
+    assert np.array_equal(hi, ehi)
+
+
 def test_device_entry_point_matches_host():
     import torch
     shape = RunShape(rows=8, cols=8, seed=9)

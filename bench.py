@@ -165,10 +165,10 @@ class Clocks:
 # warp-instructions per island-generation (sm__inst_executed_pipe_alu.sum / islands; each
 # occupies the ALU pipe two cycles) and FMA-heavy pipe cycles per island-generation
 # (sm__pipe_fmaheavy_cycles_active.sum / islands).
-ISLAND_STEP_TRAFFIC = {"kernel": "island_units_kernel<32,5,0>", "bytes": 447.8e6,
-                       "inst_per_island_gen": 42958848 / 262144,
-                       "alu_inst_per_island_gen": 13664256 / 262144,
-                       "fma_cycles_per_island_gen": 32571392 / 262144,
+ISLAND_STEP_TRAFFIC = {"kernel": "island_units_kernel<32,5,0>", "bytes": 448.1e6,
+                       "inst_per_island_gen": 36143104 / 262144,
+                       "alu_inst_per_island_gen": 14254080 / 262144,
+                       "fma_cycles_per_island_gen": 30867456 / 262144,
                        "rows": 512, "cols": 1024, "island_size": 32}
 # warp-instructions per island-generation of the resident kernel on the 32x32 torus
 # (smsp__inst_executed.sum of a 200-generation launch / (1,024 islands x 200), this build)

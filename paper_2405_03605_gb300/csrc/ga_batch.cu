@@ -113,7 +113,10 @@ __global__ void __launch_bounds__(256, (N >= 64 ? 6 : 8)) batch_units_kernel(con
     __shared__ RunParams s_r;
     __shared__ uint32_t s_unit;
     stage_params(a, s_r, s_unit);
-    step_units<N, TS, units_per_block<N>()>(s_r, a.rk, s_unit);
+    // the unit loop unrolled for the compiled-in tournament size only: with the run's
+    // parameters read from shared memory the unrolled run-time-size body spills (146.6 against
+    // 152.2e9 agent-gens/s on the 256-run mix)
+    step_units<N, TS, units_per_block<N>(), 0, TS == 5>(s_r, a.rk, s_unit);
 }
 
 __global__ void batch_sites_kernel(const RunDesc *__restrict__ runs, uint32_t n_runs,

@@ -240,9 +240,12 @@ resident_kernel(const ResidentArgs a)
                 uint4 *mine = box + static_cast<size_t>(bk_isl) * 4u + md;
                 const unsigned long long t0 = global_ns();
                 for (uint32_t polls = 0;; ++polls) {
+                    // the abort word is read beside the mailbox, not after it: a poll that
+                    // finds nothing costs one round trip to L2, not two
                     imm = read128(mine);
+                    const uint32_t ab = ld_relaxed_u32(a.abort_word);
                     if (imm.y == g) break;
-                    if (ld_relaxed_u32(a.abort_word) != 0u) {
+                    if (ab != 0u) {
                         s_abort = 1;
                         break;
                     }
@@ -299,10 +302,11 @@ resident_kernel(const ResidentArgs a)
 // One island per warp (32 and 64 agents), no block barrier: on a migration generation g the
 // warp's lanes 0..3 compute, for direction d, the neighbour R = nb(I, d)'s own slot-(d^1)
 // birth draw (the member e_d it takes from I), and the lane holding member e_d pushes it into
-// R's mailbox for direction d^1 (one 128-bit atomic exchange); the warp then computes g's
-// birth draws while those writes reach L2; lanes 0..3 poll the island's four mailboxes until
-// each holds the record of generation g, resolve the landing slots (the partial Fisher-Yates
-// draw of the synchronous mode, from the island's own slot-0..3 draws) and every lane takes
+// R's mailbox for direction d^1 (one 128-bit atomic exchange); while those writes reach L2
+// the warp computes g's birth draws, the landing slots (the partial Fisher-Yates draw of the
+// synchronous mode, from the island's own slot-0..3 draws) and the next migration
+// generation's emigrant draws, none of which needs an arrival; lanes 0..3 then poll the
+// island's four mailboxes until each holds the record of generation g, and every lane takes
 // the arrival meant for its slot by shuffles.  Warps never wait for one another inside a
 // block; each poll is bounded as in resident_kernel, and a warp that sees the abort word
 // leaves.
@@ -340,59 +344,41 @@ resident_warp_kernel(const ResidentArgs a)
         rec[ag][2] = v.z;
         rec[ag][3] = v.w;
     }
+    // the member the neighbour in direction d draws from this island at migration generation
+    // gm (lanes 0..3; every lane computes it, so the draw is not a divergent branch and can
+    // overlap other work): it depends on no state, so it is drawn a migration ahead
+    auto emigrant = [&](uint32_t gm) {
+        const uint32_t un = philox_rk(gm, nb, (d ^ 1u) | (kBirth << 16), p.run_id, a.rk).w;
+        return (((un >> 8) & 0xFFu) * N) >> 8;
+    };
+    uint32_t nd[4];
+#pragma unroll
+    for (int dd = 0; dd < 4; ++dd) nd[dd] = __shfl_sync(0xffffffffu, nb, dd);
     uint32_t gm = next_migration(p.g0, end, a.every_k, a.per_neighbor);
+    uint32_t e = emigrant(gm);
     bool aborted = false;
     for (uint32_t it = 0; it < p.n_gens; ++it) {
         const uint32_t g = p.g0 + it;
         uint4 w[A];
         if (g == gm) {
             uint4 *box = a.mail + static_cast<size_t>((g / a.every_k) & 1u) * p.n_islands * 4u;
-            // sends: the member the neighbour in direction d draws from this island
-            uint32_t e = 0;
-            if (dir_lane) {
-                const uint32_t un = philox_rk(g, nb, (d ^ 1u) | (kBirth << 16), p.run_id, a.rk).w;
-                e = (((un >> 8) & 0xFFu) * N) >> 8;
-            }
+            // sends: lane holding the member e_d pushes it to the neighbour in direction d
 #pragma unroll
             for (int dd = 0; dd < 4; ++dd) {
                 const uint32_t ed = __shfl_sync(0xffffffffu, e, dd);
-                const uint32_t nd = __shfl_sync(0xffffffffu, nb, dd);
 #pragma unroll
                 for (int ag = 0; ag < A; ++ag) {
                     if (lane + 32u * ag == ed && island != a.drop_island &&
-                        in_bounds(nd < p.n_islands, p.status))
-                        write128(box + static_cast<size_t>(nd) * 4u + (static_cast<uint32_t>(dd) ^ 1u),
+                        in_bounds(nd[dd] < p.n_islands, p.status))
+                        write128(box + static_cast<size_t>(nd[dd]) * 4u + (static_cast<uint32_t>(dd) ^ 1u),
                                  make_uint4(rec[ag][0], rec[ag][1], rec[ag][2], rec[ag][3]));
                 }
             }
-            // this generation's birth draws, while the neighbours' writes travel
+            // while the neighbours' writes travel: the next migration's emigrant draws, this
+            // generation's birth draws and the landing slots, none of which needs an arrival
+            const uint32_t gm_next = next_migration(g + 1u, end, a.every_k, a.per_neighbor);
+            const uint32_t e_next = emigrant(gm_next);
             birth_draws<N>(w, p, a.rk, g, island, lane);
-            // receives: lanes 0..3 wait for the records of generation g
-            uint4 imm = make_uint4(0u, 0u, 0u, 0u);
-            bool gave_up = false;
-            if (dir_lane) {
-                uint4 *mine = box + static_cast<size_t>(island) * 4u + d;
-                const unsigned long long t0 = global_ns();
-                for (uint32_t polls = 0;; ++polls) {
-                    imm = read128(mine);
-                    if (imm.y == g) break;
-                    if (ld_relaxed_u32(a.abort_word) != 0u) {
-                        gave_up = true;
-                        break;
-                    }
-                    if (global_ns() - t0 > a.wait_ns) {
-                        atomicCAS(p.status, 0, GA_ETIMEOUT);
-                        atomicExch(a.abort_word, 1u);
-                        gave_up = true;
-                        break;
-                    }
-                    if (polls >= 8u) __nanosleep(64);
-                }
-            }
-            if (__any_sync(0xffffffffu, gave_up)) {
-                aborted = true;
-                break;
-            }
             // landing slots: partial Fisher-Yates over [0, N) in direction order from slot d's
             // own draw (word 3 of lane d's first birth draw), the same on every lane
             const uint32_t u = __shfl_sync(0xffffffffu, w[0].w, static_cast<int>(d));
@@ -412,21 +398,53 @@ resident_warp_kernel(const ResidentArgs a)
                 slot[dd] = vr;
                 v[dd] = vd;
             }
-            const uint32_t im[4] = {imm.x, imm.y, imm.z, imm.w};
+            int from[A];
 #pragma unroll
             for (int ag = 0; ag < A; ++ag) {
                 const uint32_t mine = lane + 32u * ag;
-                int from = -1;
+                from[ag] = -1;
 #pragma unroll
                 for (int dd = 0; dd < 4; ++dd)
-                    if (slot[dd] == mine) from = dd;
-#pragma unroll
-                for (int k = 0; k < LW; ++k) {
-                    const uint32_t val = __shfl_sync(0xffffffffu, im[k], from < 0 ? 0 : from);
-                    if (from >= 0) rec[ag][k] = val;
+                    if (slot[dd] == mine) from[ag] = dd;
+            }
+            // receives: lanes 0..3 wait for the records of generation g
+            uint4 imm = make_uint4(0u, 0u, 0u, 0u);
+            bool gave_up = false;
+            if (dir_lane) {
+                uint4 *mine = box + static_cast<size_t>(island) * 4u + d;
+                const unsigned long long t0 = global_ns();
+                for (uint32_t polls = 0;; ++polls) {
+                    imm = read128(mine);  // the abort word beside it, as in resident_kernel
+                    const uint32_t ab = ld_relaxed_u32(a.abort_word);
+                    if (imm.y == g) break;
+                    if (ab != 0u) {
+                        gave_up = true;
+                        break;
+                    }
+                    if (global_ns() - t0 > a.wait_ns) {
+                        atomicCAS(p.status, 0, GA_ETIMEOUT);
+                        atomicExch(a.abort_word, 1u);
+                        gave_up = true;
+                        break;
+                    }
+                    if (polls >= 8u) __nanosleep(64);
                 }
             }
-            gm = next_migration(g + 1u, end, a.every_k, a.per_neighbor);
+            if (__any_sync(0xffffffffu, gave_up)) {
+                aborted = true;
+                break;
+            }
+            const uint32_t im[4] = {imm.x, imm.y, imm.z, imm.w};
+#pragma unroll
+            for (int ag = 0; ag < A; ++ag) {
+#pragma unroll
+                for (int k = 0; k < LW; ++k) {
+                    const uint32_t val = __shfl_sync(0xffffffffu, im[k], from[ag] < 0 ? 0 : from[ag]);
+                    if (from[ag] >= 0) rec[ag][k] = val;
+                }
+            }
+            gm = gm_next;
+            e = e_next;
         } else {
             birth_draws<N>(w, p, a.rk, g, island, lane);
         }

@@ -96,3 +96,26 @@ def test_outputs_at_any_4_byte_alignment():
     elo, ehi = o.mrca_bounds(ids)
     assert np.array_equal(lo.cpu().numpy().view(np.uint32), elo)
     assert np.array_equal(hi.cpu().numpy().view(np.uint32), ehi)
+
+
+@pytest.mark.parametrize("n_ids", [2, 5, 333, 1500])
+def test_output_alignment(n_ids):
+    """(lo, hi) arrays at any 4-byte offset (not only the 256-byte boundaries of fresh
+    allocations): the bounds equal the oracle's and nothing outside the n(n-1)/2 pairs is
+    written."""
+    import torch
+    shape = RunShape(rows=8, cols=8, seed=13)
+    g, o, ids = both(shape, 300, n_ids, seed=n_ids)
+    d_ids = torch.from_numpy(ids.view(np.int32)).cuda()
+    pairs = n_ids * (n_ids - 1) // 2
+    elo, ehi = o.mrca_bounds(ids)
+    for off_lo, off_hi in ((0, 0), (1, 1), (2, 0), (0, 3), (3, 2)):
+        lo_b = torch.full((pairs + 8,), -1, dtype=torch.int32, device="cuda")
+        hi_b = torch.full((pairs + 8,), -1, dtype=torch.int32, device="cuda")
+        lo, hi = lo_b[off_lo:off_lo + pairs], hi_b[off_hi:off_hi + pairs]
+        g.mrca_bounds_device(d_ids, lo, hi)
+        g.sync()
+        assert np.array_equal(lo.cpu().numpy().view(np.uint32), elo)
+        assert np.array_equal(hi.cpu().numpy().view(np.uint32), ehi)
+        for buf, off in ((lo_b, off_lo), (hi_b, off_hi)):
+            assert bool((buf[:off] == -1).all()) and bool((buf[off + pairs:] == -1).all())

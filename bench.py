@@ -172,7 +172,7 @@ ISLAND_STEP_TRAFFIC = {"kernel": "island_units_kernel<32,5,0>", "bytes": 448.1e6
                        "rows": 512, "cols": 1024, "island_size": 32}
 # warp-instructions per island-generation of the resident kernel on the 32x32 torus
 # (smsp__inst_executed.sum of a 200-generation launch / (1,024 islands x 200), this build)
-RESIDENT_INST = {"kernel": "resident_warp_kernel<32,5,0,4>", "inst_per_island_gen": 73490768 / 204800}
+RESIDENT_INST = {"kernel": "resident_warp_kernel<32,5,0,4>", "inst_per_island_gen": 70550765 / 204800}
 
 
 def aggregate_replicas(elapsed_ms, agent_gens, world, device="cpu"):

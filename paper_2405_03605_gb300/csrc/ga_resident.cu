@@ -305,9 +305,11 @@ resident_kernel(const ResidentArgs a)
 // R's mailbox for direction d^1 (one 128-bit atomic exchange); while those writes reach L2
 // the warp computes g's birth draws, the landing slots (the partial Fisher-Yates draw of the
 // synchronous mode, from the island's own slot-0..3 draws) and the next migration
-// generation's emigrant draws, none of which needs an arrival; lanes 0..3 then poll the
-// island's four mailboxes until each holds the record of generation g, and every lane takes
-// the arrival meant for its slot by shuffles.  Warps never wait for one another inside a
+// generation's emigrant draws, none of which needs an arrival; lanes 0..3 read the island's
+// four mailboxes once right after the pushes (that read travels while the warp draws, so an
+// island whose neighbours got to g first has their records without a further round trip),
+// then poll until each holds the record of generation g, and every lane takes the arrival
+// meant for its slot by shuffles.  Warps never wait for one another inside a
 // block; each poll is bounded as in resident_kernel, and a warp that sees the abort word
 // leaves.
 template <int N, int TS, int MODEL, int WARPS>
@@ -359,6 +361,7 @@ resident_warp_kernel(const ResidentArgs a)
     bool aborted = false;
     for (uint32_t it = 0; it < p.n_gens; ++it) {
         const uint32_t g = p.g0 + it;
+        const uint2 dm = gen_mask_at(p, it);  // the generation's deposit masks, read up front
         uint4 w[A];
         if (g == gm) {
             uint4 *box = a.mail + static_cast<size_t>((g / a.every_k) & 1u) * p.n_islands * 4u;
@@ -374,6 +377,12 @@ resident_warp_kernel(const ResidentArgs a)
                                  make_uint4(rec[ag][0], rec[ag][1], rec[ag][2], rec[ag][3]));
                 }
             }
+            // an early read of the island's own mailboxes: an island that reaches g after its
+            // neighbours (the one that sets the pace) usually finds their records already there,
+            // and this read returns while the warp draws instead of after
+            uint4 *mine = box + static_cast<size_t>(island) * 4u + d;
+            uint4 early = make_uint4(0u, 0u, 0u, 0u);
+            if (dir_lane) early = read128(mine);
             // while the neighbours' writes travel: the next migration's emigrant draws, this
             // generation's birth draws and the landing slots, none of which needs an arrival
             const uint32_t gm_next = next_migration(g + 1u, end, a.every_k, a.per_neighbor);
@@ -408,10 +417,9 @@ resident_warp_kernel(const ResidentArgs a)
                     if (slot[dd] == mine) from[ag] = dd;
             }
             // receives: lanes 0..3 wait for the records of generation g
-            uint4 imm = make_uint4(0u, 0u, 0u, 0u);
+            uint4 imm = early;
             bool gave_up = false;
-            if (dir_lane) {
-                uint4 *mine = box + static_cast<size_t>(island) * 4u + d;
+            if (dir_lane && imm.y != g) {
                 const unsigned long long t0 = global_ns();
                 for (uint32_t polls = 0;; ++polls) {
                     imm = read128(mine);  // the abort word beside it, as in resident_kernel
@@ -448,8 +456,7 @@ resident_warp_kernel(const ResidentArgs a)
         } else {
             birth_draws<N>(w, p, a.rk, g, island, lane);
         }
-        reproduce<N, 2, TS, MODEL, 0, 1>(rec, w, p, a.rk, island, lane, 0xffffffffu, g, 0,
-                                         gen_mask_at(p, it));
+        reproduce<N, 2, TS, MODEL, 0, 1>(rec, w, p, a.rk, island, lane, 0xffffffffu, g, 0, dm);
     }
     if (!aborted) {
 #pragma unroll
